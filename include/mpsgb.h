@@ -1,0 +1,184 @@
+/* mpsgb -- grouped-qubit MPS TEBD of the 2D transverse-field Ising model on one GB300.
+ *
+ * C ABI of the CUDA library (libmpsgb.so).  Method: Mandra et al., "A Heuristic for
+ * Matrix Product State Simulation of Out-of-Equilibrium Dynamics of Two-Dimensional
+ * Quantum Spin Systems":
+ *   Sec. II   Eq. hamiltonian  H = J sum_<ij> Z_i Z_j + h sum_i X_i (periodic square lattice)
+ *             Eq. trotter_step U(dt) = e^{-i dt H_X/2} e^{-i dt H_ZZ} e^{-i dt H_X/2}
+ *             Eq. initial_state prod_j (cos(theta/2)|0> + sin(theta/2)|1>), theta = theta_min + dtheta
+ *             Eq. z2_tot  <Z_tot^2> = (1/n^2) sum_{j,k} <Z_j Z_k>
+ *   Sec. III  TEBD on a grouped-qubit MPS (each row split in two groups fused into one
+ *             block, snake order); in-block gates update one block; inter-block gates act
+ *             as rank-2 MPOs that double the spanned bonds, which are truncated back to
+ *             chi by SVD with the orthogonality centre on the bond; the state is
+ *             renormalised after each truncation and F_MPS is the product of the
+ *             truncation fidelities; Eq. Z_tot; Eq. Z_tot_via_F; Eq. z2_tot_rescaled;
+ *             Table gamma_scaling.
+ *
+ * Conventions
+ *   - Qubit (r, c) of an Lx x Ly grid has index r*Ly + c; |0> is Z = +1.
+ *   - Gate angles are literal: the X layer is prod_j exp(-i alpha X_j), the ZZ layer
+ *     prod_<ij> exp(-i phi Z_i Z_j) (phi = J dt; alpha = h dt/2 for second order).
+ *   - Every function returns an mpsgb_status (0 on success).  On failure the message of
+ *     mpsgb_last_error() (per calling thread) says what went wrong.  No exception or
+ *     CUDA error crosses the ABI; a CUDA error reports MPSGB_EDEVICE.
+ *   - Ownership: a handle owns all device memory of its MPS (blocks and workspace) and
+ *     frees it in mpsgb_destroy.  The CUDA stream and the allocator passed at creation
+ *     are borrowed and must outlive the handle.  Output pointers are caller-owned host
+ *     memory.  Calls on one handle are not thread-safe; distinct handles are.
+ *   - Device waits inside the library are bounded; none spins without a limit.
+ */
+#ifndef MPSGB_H
+#define MPSGB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpsgb_mps* mpsgb_handle;
+
+typedef enum {
+  MPSGB_OK = 0,
+  MPSGB_EINVAL = -1,    /* bad argument (size, enum, NaN angle, null pointer) */
+  MPSGB_ENOMEM = -2,    /* the allocator returned NULL */
+  MPSGB_ETIMEDOUT = -3, /* a bounded device wait ran out */
+  MPSGB_EDEVICE = -4,   /* a CUDA call failed */
+  MPSGB_ESTATE = -5     /* the handle is in a state that does not allow the call */
+} mpsgb_status;
+
+/* Arithmetic of the path.
+ *   FP64         complex128 storage, every contraction and the truncation core in FP64.
+ *   SPLIT_TF32X3 complex64 storage; block-sized contractions as 3-term TF32 split products
+ *                on the tensor cores with FP32 accumulation; truncation weights and F in FP64.
+ *   SPLIT_BF16X3 as above with 3-term BF16 splits.
+ *   FP32         complex64 storage, all contractions on FP32 CUDA cores (reference form for
+ *                the split forms). */
+typedef enum { MPSGB_FP64 = 0, MPSGB_SPLIT_TF32X3 = 1, MPSGB_SPLIT_BF16X3 = 2, MPSGB_FP32 = 3 } mpsgb_precision;
+/* Non-adjacent gates: MPO route (Sec. III) or SWAP routing. */
+typedef enum { MPSGB_ROUTE_MPO = 0, MPSGB_ROUTE_SWAP = 1 } mpsgb_route;
+typedef enum { MPSGB_LAYER_X = 0, MPSGB_LAYER_ZZ = 1 } mpsgb_layer;
+typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2 } mpsgb_obs;
+
+typedef struct {
+  int Lx, Ly;          /* grid: Lx rows of Ly qubits, periodic in both directions; 2..16 each, n <= 256 */
+  int chi_max;         /* maximum bond dimension chi (>= 1) */
+  double theta;        /* absolute initial angle of Eq. initial_state (use mpsgb_initial_theta) */
+  mpsgb_precision prec;
+  mpsgb_route route;
+  unsigned long long seed; /* recorded only: the method draws no random numbers */
+  double J, h, dt;     /* evolution parameters used by mpsgb_batch_step */
+  int trotter_order;   /* 1: X then ZZ per step; 2: Eq. trotter_step */
+} mpsgb_config;
+
+/* Device allocator used for every allocation of a handle.  alloc returns NULL on failure.
+ * Pass NULL to mpsgb_create to use cudaMallocAsync / cudaFreeAsync on the handle's stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} mpsgb_allocator;
+
+/* Create the product state of Eq. initial_state with all bonds 1 and F_MPS = 1.
+ * cfg: read only, copied.  alloc: borrowed or NULL.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream) on which all work of the handle is issued.  *out receives the handle.
+ * Errors: EINVAL for an unsupported grid / chi / precision, ENOMEM, EDEVICE. */
+int mpsgb_create(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* cuda_stream, mpsgb_handle* out);
+
+/* Apply one Trotter layer (Sec. III): LAYER_X applies prod_j exp(-i angle X_j) block by block
+ * (no truncation); LAYER_ZZ applies prod_<ij> exp(-i angle Z_i Z_j): in-block pairs as diagonal
+ * phases, then every inter-block gate, in the fixed order of the schedule, as a rank-2 MPO
+ * followed by truncation of each spanned bond to chi_max; F_MPS is multiplied by each
+ * truncation fidelity.  Errors: EINVAL (NaN angle / bad layer), EDEVICE. */
+int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle);
+
+/* nsteps Trotter steps: order 2 = X(h dt/2) ZZ(J dt) X(h dt/2) (Eq. trotter_step), order 1 =
+ * X(h dt) then ZZ(J dt).  Equivalent to the corresponding apply_layer calls. */
+int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order, int nsteps);
+
+/* Re-compress the whole MPS to bond dimension chi <= chi_max by a left-to-right sequential SVD
+ * sweep; multiplies F_MPS by every truncation fidelity.  Errors: EINVAL for chi < 1 or > chi_max. */
+int mpsgb_truncate(mpsgb_handle h, int chi);
+
+/* Expectation value (Eq. Z_tot, Eq. z2_tot, or <X_tot> = (1/n) sum_j <X_j>) of the current,
+ * normalised MPS, written to the host double *out.  Synchronises the handle's stream. */
+int mpsgb_expect(mpsgb_handle h, mpsgb_obs obs, double* out);
+
+/* All three observables and the squared norm in one environment sweep:
+ * out[0] = <Z_tot>, out[1] = <Z_tot^2>, out[2] = <X_tot>, out[3] = <psi|psi>. Host pointer. */
+int mpsgb_observables(mpsgb_handle h, double out[4]);
+
+/* F_MPS (Sec. III), the product of all truncation fidelities so far, to the host double *F. */
+int mpsgb_fidelity(mpsgb_handle h, double* F);
+
+/* Schmidt values across bond `bond` (0 .. nblocks-2, between blocks bond and bond+1), descending,
+ * written to out[0 .. min(cap, n)-1]; *n receives the bond dimension.  Moves the orthogonality
+ * centre (the state is unchanged).  Errors: EINVAL for a bad bond or null pointer. */
+int mpsgb_singular_values(mpsgb_handle h, int bond, double* out, int cap, int* n);
+
+/* Current bond dimensions (nblocks-1 values) to out[0 .. cap-1]; *n receives nblocks-1. */
+int mpsgb_bond_dims(mpsgb_handle h, int* out, int cap, int* n);
+
+/* Device memory a handle of this config holds for its blocks, chi^2 * dmax * nblocks * element
+ * size (the admission figure of the serving loop), to the host *bytes.  Host only. */
+int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes);
+
+/* Advance `count` independent handles by nsteps Trotter steps each with the J, h, dt and order of
+ * their configs; handles are advanced concurrently (one host thread per handle, each on its own
+ * stream).  flags: reserved, pass 0.  Returns the first failing status. */
+int mpsgb_batch_step(mpsgb_handle* hs, int count, int nsteps, int flags);
+
+/* Write / read a checkpoint: config, bond dims, centre, F_MPS, counters and all blocks.
+ * mpsgb_load creates a new handle (alloc and stream as in mpsgb_create).  Errors: EINVAL for an
+ * unreadable or mismatched file, ENOMEM, EDEVICE. */
+int mpsgb_save(mpsgb_handle h, const char* path);
+int mpsgb_load(const char* path, const mpsgb_allocator* alloc, void* cuda_stream, mpsgb_handle* out);
+
+/* Free the handle and all its device memory (synchronises its stream).  NULL is ignored. */
+void mpsgb_destroy(mpsgb_handle h);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char* mpsgb_last_error(void);
+
+/* Counters of a handle: out[0] bond truncations, out[1] inter-block gates, out[2] centre moves,
+ * out[3] eigensolver calls, out[4] eigensolver sweeps.  Host pointer, 5 entries. */
+int mpsgb_stats(mpsgb_handle h, long long out[5]);
+
+/* Number of CUDA kernels the library has launched in this process (all handles). */
+unsigned long long mpsgb_launch_count(void);
+
+/* Device-time measurement of the library's launch sites with CUDA events on their own streams.
+ * mpsgb_kernel_timing(1) resets the totals and starts recording (0 stops); mpsgb_kernel_times
+ * synchronises on the recorded events and returns, for launch site `site` (0 .. 6, see
+ * mpsgb_kernel_site_name), the summed device time in ms, the launch count and the useful work of
+ * those launches (real flops for arithmetic sites, bytes moved for the in-block gate site).
+ * Recording adds two event records per launch; it is off by default. */
+int mpsgb_kernel_timing(int enable);
+int mpsgb_kernel_times(int site, double* ms, long long* launches, double* work);
+const char* mpsgb_kernel_site_name(int site);
+
+/* Host-only schedule facts of an Lx x Ly grid (no GPU needed): out[0] blocks, out[1] ZZ bonds,
+ * out[2] in-block bonds, out[3] inter-block gates, out[4] bond truncations per ZZ layer,
+ * out[5] largest local dimension.  Errors: EINVAL for an unsupported grid. */
+int mpsgb_schedule_info(int Lx, int Ly, long long out[6]);
+
+/* Host-only: the inter-block gates of the ZZ layer in application order, 6 ints each
+ * (p, q, qubit_i, qubit_j, bit_i, bit_j), at most cap gates; *n receives the gate count. */
+int mpsgb_schedule_gates(int Lx, int Ly, int* out, int cap, int* n);
+
+/* Host-only: theta_min + dtheta with theta_min = asin(h / (4 J)) (Sec. II). */
+double mpsgb_initial_theta(double J, double hx, double dtheta);
+
+/* Host-only: gamma_fit = a log2(chi)/n + b of Table gamma_scaling; temperature 0 = low
+ * (dtheta = 0), 1 = mid (2 pi/9), 2 = high (3 pi/9).  Returns NaN for another temperature. */
+double mpsgb_gamma_fit(int temperature, int chi, int n);
+
+/* Host-only rescaling (Eq. Z_tot_via_F and Eq. z2_tot_rescaled): out[0] = F * z,
+ * out[1] = z2 * F^gamma. */
+int mpsgb_rescale(double z, double z2, double F, double gamma, double out[2]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPSGB_H */

@@ -42,14 +42,16 @@ class MPS:
     """Grouped-qubit MPS with an explicit orthogonality centre (a block index)."""
 
     def __init__(self, Lx, Ly, chi, theta):
+        """theta: the angle of Eq. initial_state, or one angle per qubit (index r * Ly + c)."""
         self.Lx, self.Ly, self.chi = Lx, Ly, chi
         self.layout = layout.blocks(Lx, Ly)
         self.n = Lx * Ly
-        v = np.array([np.cos(theta / 2.0), np.sin(theta / 2.0)], dtype=np.complex128)
+        thetas = np.broadcast_to(np.asarray(theta, dtype=np.float64), (self.n,))
         self.blocks = []
         for b in self.layout:
             phys = np.ones(1, dtype=np.complex128)
-            for _ in b["qubits"]:
+            for q in b["qubits"]:
+                v = np.array([np.cos(thetas[q] / 2.0), np.sin(thetas[q] / 2.0)], dtype=np.complex128)
                 phys = np.kron(phys, v)  # first qubit = most significant bit
             self.blocks.append(phys.reshape(1, b["d"], 1).copy())
         self.centre = 0
@@ -256,9 +258,12 @@ def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False):
     alpha, phi = model.layer_angles(J, h, dt, order)
     intra, inter = layout.schedule(Lx, Ly)
     psi = MPS(Lx, Ly, chi, theta)
-    rec = {"Z": [], "Z2": [], "X": [], "F": [], "spectra": []}
+    rec = {"Z": [], "Z2": [], "X": [], "F": [], "spectra": [], "gap": []}
 
     def record():
+        # smallest relative gap at any cut since the previous record (inf if nothing was cut)
+        rec["gap"].append(min(psi.cut_gaps) if psi.cut_gaps else float("inf"))
+        psi.cut_gaps = []
         z, z2, x, _ = psi.observables()
         rec["Z"].append(z)
         rec["Z2"].append(z2)
@@ -280,7 +285,7 @@ def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False):
     out["spectra"] = rec["spectra"]
     out["fidelities"] = np.array(psi.fidelities)
     out["kept_norms"] = np.array(psi.kept_norms)
-    out["min_cut_gap"] = min(psi.cut_gaps) if psi.cut_gaps else float("inf")
+    out["min_cut_gap"] = float(np.min(out["gap"]))
     out["bond_dims"] = psi.bond_dims()
     out["mps"] = psi
     return out

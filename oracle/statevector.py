@@ -27,12 +27,13 @@ def _z_values(n):
 
 
 def product_state(n, theta):
-    """Eq. initial_state as a dense vector."""
+    """Eq. initial_state as a dense vector (theta: one angle, or one per qubit)."""
     if n > MAX_QUBITS:
         raise ValueError("state vector limited to %d qubits" % MAX_QUBITS)
-    v = np.array([np.cos(theta / 2.0), np.sin(theta / 2.0)], dtype=np.complex128)
+    thetas = np.broadcast_to(np.asarray(theta, dtype=np.float64), (n,))
     psi = np.ones(1, dtype=np.complex128)
-    for _ in range(n):
+    for q in range(n):
+        v = np.array([np.cos(thetas[q] / 2.0), np.sin(thetas[q] / 2.0)], dtype=np.complex128)
         psi = np.kron(psi, v)
     return psi
 

@@ -1,0 +1,275 @@
+// C ABI of libmpsgb (declared in include/mpsgb.h): argument checks, handle
+// ownership, exception-to-status conversion and the host-only helpers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mpsgb.h"
+#include "engine.hpp"
+
+using mpsgb::Engine;
+using mpsgb::Fail;
+
+struct mpsgb_mps {
+  Engine* e = nullptr;
+};
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int status, const std::string& msg) {
+  g_err = msg;
+  return status;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const Fail& x) {
+    return fail(x.status, x.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(MPSGB_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(MPSGB_EDEVICE, "unexpected internal error");
+  }
+}
+
+int check_config(const mpsgb_config* c) {
+  if (!c) return fail(MPSGB_EINVAL, "null config");
+  if (c->prec < MPSGB_FP64 || c->prec > MPSGB_FP32) return fail(MPSGB_EINVAL, "unknown precision");
+  if (c->route != MPSGB_ROUTE_MPO && c->route != MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "unknown route");
+  if (c->route == MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "SWAP routing is not available in this build");
+  if (!std::isfinite(c->theta)) return fail(MPSGB_EINVAL, "theta is not finite");
+  if (c->chi_max < 1 || c->chi_max > 8192) return fail(MPSGB_EINVAL, "chi_max must be in 1..8192");
+  mpsgb::Layout L;
+  std::string err;
+  if (!mpsgb::make_layout(c->Lx, c->Ly, L, err)) return fail(MPSGB_EINVAL, err);
+  return MPSGB_OK;
+}
+
+int create_impl(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* stream, mpsgb_handle* out) {
+  if (!out) return fail(MPSGB_EINVAL, "null output handle");
+  *out = nullptr;
+  int s = check_config(cfg);
+  if (s) return s;
+  std::string err;
+  int status = 0;
+  Engine* e = mpsgb::make_engine(*cfg, alloc, (cudaStream_t)stream, err, status);
+  if (!e) return fail(status ? status : MPSGB_EDEVICE, err);
+  auto* h = new mpsgb_mps();
+  h->e = e;
+  *out = h;
+  return MPSGB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mpsgb_create(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* cuda_stream, mpsgb_handle* out) {
+  return guarded([&]() -> int { return create_impl(cfg, alloc, cuda_stream, out); });
+}
+
+int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle) {
+  if (!h || !h->e) return fail(MPSGB_EINVAL, "null handle");
+  if (!std::isfinite(angle)) return fail(MPSGB_EINVAL, "angle is not finite");
+  if (layer != MPSGB_LAYER_X && layer != MPSGB_LAYER_ZZ) return fail(MPSGB_EINVAL, "unknown layer");
+  return guarded([&]() -> int { return layer == MPSGB_LAYER_X ? h->e->apply_x(angle) : h->e->apply_zz(angle); });
+}
+
+int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order, int nsteps) {
+  if (!h || !h->e) return fail(MPSGB_EINVAL, "null handle");
+  if (!std::isfinite(J) || !std::isfinite(hx) || !std::isfinite(dt)) return fail(MPSGB_EINVAL, "parameter is not finite");
+  if (trotter_order != 1 && trotter_order != 2) return fail(MPSGB_EINVAL, "trotter_order must be 1 or 2");
+  if (nsteps < 0) return fail(MPSGB_EINVAL, "nsteps must be >= 0");
+  return guarded([&]() -> int { return h->e->step(J, hx, dt, trotter_order, nsteps); });
+}
+
+int mpsgb_truncate(mpsgb_handle h, int chi) {
+  if (!h || !h->e) return fail(MPSGB_EINVAL, "null handle");
+  return guarded([&]() -> int { return h->e->truncate(chi); });
+}
+
+int mpsgb_observables(mpsgb_handle h, double out[4]) {
+  if (!h || !h->e || !out) return fail(MPSGB_EINVAL, "null argument");
+  return guarded([&]() -> int { return h->e->observables(out); });
+}
+
+int mpsgb_expect(mpsgb_handle h, mpsgb_obs obs, double* out) {
+  if (!h || !h->e || !out) return fail(MPSGB_EINVAL, "null argument");
+  if (obs < MPSGB_Z_TOT || obs > MPSGB_X_TOT) return fail(MPSGB_EINVAL, "unknown observable");
+  double v[4];
+  int s = mpsgb_observables(h, v);
+  if (s) return s;
+  *out = v[(int)obs];
+  return MPSGB_OK;
+}
+
+int mpsgb_fidelity(mpsgb_handle h, double* F) {
+  if (!h || !h->e || !F) return fail(MPSGB_EINVAL, "null argument");
+  *F = h->e->F;
+  return MPSGB_OK;
+}
+
+int mpsgb_singular_values(mpsgb_handle h, int bond, double* out, int cap, int* n) {
+  if (!h || !h->e || !n || (cap > 0 && !out)) return fail(MPSGB_EINVAL, "null argument");
+  return guarded([&]() -> int {
+    std::vector<double> s;
+    int st = h->e->singular_values(bond, s);
+    if (st) return st;
+    *n = (int)s.size();
+    for (int i = 0; i < cap && i < (int)s.size(); ++i) out[i] = s[i];
+    return MPSGB_OK;
+  });
+}
+
+int mpsgb_bond_dims(mpsgb_handle h, int* out, int cap, int* n) {
+  if (!h || !h->e || !n || (cap > 0 && !out)) return fail(MPSGB_EINVAL, "null argument");
+  const auto& d = h->e->dims;
+  *n = (int)d.size();
+  for (int i = 0; i < cap && i < (int)d.size(); ++i) out[i] = d[i];
+  return MPSGB_OK;
+}
+
+int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes) {
+  if (!bytes) return fail(MPSGB_EINVAL, "null argument");
+  int s = check_config(cfg);
+  if (s) return s;
+  mpsgb::Layout L;
+  std::string err;
+  mpsgb::make_layout(cfg->Lx, cfg->Ly, L, err);
+  double mb = 1;
+  for (double b : L.bound) mb = std::max(mb, b);
+  double chi = std::min<double>(cfg->chi_max, mb);
+  int dmax = 1;
+  for (int k : L.k) dmax = std::max(dmax, 1 << k);
+  size_t elem = cfg->prec == MPSGB_FP64 ? 16 : 8;
+  *bytes = (size_t)(chi * chi) * dmax * L.N * elem;
+  return MPSGB_OK;
+}
+
+int mpsgb_batch_step(mpsgb_handle* hs, int count, int nsteps, int flags) {
+  (void)flags;
+  if (!hs || count < 0 || nsteps < 0) return fail(MPSGB_EINVAL, "bad batch arguments");
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || !hs[i]->e) return fail(MPSGB_EINVAL, "null handle in batch");
+  std::vector<int> st(count, 0);
+  std::vector<std::string> msg(count);
+  std::vector<std::thread> th;
+  th.reserve(count);
+  for (int i = 0; i < count; ++i)
+    th.emplace_back([&, i] {
+      const mpsgb_config& c = hs[i]->e->cfg;
+      st[i] = mpsgb_step(hs[i], c.J, c.h, c.dt, c.trotter_order, nsteps);
+      if (st[i]) msg[i] = mpsgb_last_error();
+    });
+  for (auto& t : th) t.join();
+  for (int i = 0; i < count; ++i)
+    if (st[i]) return fail(st[i], "handle " + std::to_string(i) + ": " + msg[i]);
+  g_err.clear();
+  return MPSGB_OK;
+}
+
+int mpsgb_save(mpsgb_handle h, const char* path) {
+  if (!h || !h->e || !path) return fail(MPSGB_EINVAL, "null argument");
+  return guarded([&]() -> int { return h->e->save(path); });
+}
+
+int mpsgb_load(const char* path, const mpsgb_allocator* alloc, void* cuda_stream, mpsgb_handle* out) {
+  if (!path || !out) return fail(MPSGB_EINVAL, "null argument");
+  *out = nullptr;
+  return guarded([&]() -> int {
+    FILE* fh = std::fopen(path, "rb");
+    if (!fh) return fail(MPSGB_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    mpsgb_config cfg;
+    if (std::fread(magic, 1, 8, fh) != 8 || std::memcmp(magic, "MPSGBv1", 8) != 0 ||
+        std::fread(&cfg, sizeof(cfg), 1, fh) != 1) {
+      std::fclose(fh);
+      return fail(MPSGB_EINVAL, "not an mpsgb checkpoint");
+    }
+    mpsgb_handle h = nullptr;
+    int s = create_impl(&cfg, alloc, cuda_stream, &h);
+    if (s) { std::fclose(fh); return s; }
+    try {
+      h->e->load_blocks(fh);
+    } catch (...) {
+      std::fclose(fh);
+      mpsgb_destroy(h);
+      throw;
+    }
+    std::fclose(fh);
+    *out = h;
+    return MPSGB_OK;
+  });
+}
+
+void mpsgb_destroy(mpsgb_handle h) {
+  if (!h) return;
+  delete h->e;
+  delete h;
+}
+
+const char* mpsgb_last_error(void) { return g_err.c_str(); }
+
+int mpsgb_stats(mpsgb_handle h, long long out[5]) {
+  if (!h || !h->e || !out) return fail(MPSGB_EINVAL, "null argument");
+  const auto& s = h->e->stats;
+  out[0] = s.truncations; out[1] = s.gates; out[2] = s.centre_moves; out[3] = s.eig_calls; out[4] = s.eig_sweeps;
+  return MPSGB_OK;
+}
+
+unsigned long long mpsgb_launch_count(void) { return __atomic_load_n(&mpsgb::g_launch_count, __ATOMIC_RELAXED); }
+
+int mpsgb_schedule_info(int Lx, int Ly, long long out[6]) {
+  if (!out) return fail(MPSGB_EINVAL, "null argument");
+  mpsgb::Layout L;
+  std::string err;
+  if (!mpsgb::make_layout(Lx, Ly, L, err)) return fail(MPSGB_EINVAL, err);
+  long long nintra = 0, ntr = 0;
+  int dmax = 1;
+  for (auto& v : L.intra) nintra += (long long)v.size();
+  for (auto& g : L.inter) ntr += g.q - g.p;
+  for (int k : L.k) dmax = std::max(dmax, 1 << k);
+  out[0] = L.N; out[1] = nintra + (long long)L.inter.size(); out[2] = nintra;
+  out[3] = (long long)L.inter.size(); out[4] = ntr; out[5] = dmax;
+  return MPSGB_OK;
+}
+
+int mpsgb_schedule_gates(int Lx, int Ly, int* out, int cap, int* n) {
+  if (!n || (cap > 0 && !out)) return fail(MPSGB_EINVAL, "null argument");
+  mpsgb::Layout L;
+  std::string err;
+  if (!mpsgb::make_layout(Lx, Ly, L, err)) return fail(MPSGB_EINVAL, err);
+  *n = (int)L.inter.size();
+  for (int i = 0; i < cap && i < (int)L.inter.size(); ++i) {
+    const auto& g = L.inter[i];
+    int v[6] = {g.p, g.q, g.qi, g.qj, g.ti, g.tj};
+    for (int j = 0; j < 6; ++j) out[6 * i + j] = v[j];
+  }
+  return MPSGB_OK;
+}
+
+double mpsgb_initial_theta(double J, double hx, double dtheta) { return std::asin(hx / (4.0 * J)) + dtheta; }
+
+double mpsgb_gamma_fit(int temperature, int chi, int n) {
+  // Table gamma_scaling: (a, b) for low / mid / high
+  static const double a[3] = {2.588, 1.8252, 1.641};
+  static const double b[3] = {0.0, 0.0, -0.1298};
+  if (temperature < 0 || temperature > 2 || chi < 1 || n < 1) return std::nan("");
+  return a[temperature] * std::log2((double)chi) / n + b[temperature];
+}
+
+int mpsgb_rescale(double z, double z2, double F, double gamma, double out[2]) {
+  if (!out) return fail(MPSGB_EINVAL, "null argument");
+  out[0] = F * z;
+  out[1] = z2 * std::pow(F, gamma);
+  return MPSGB_OK;
+}
+
+}  // extern "C"

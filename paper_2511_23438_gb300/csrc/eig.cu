@@ -1,0 +1,401 @@
+// Hermitian eigensolver: cyclic parallel (round-robin) two-sided Jacobi.
+//
+// n <= 32 : one warp per matrix, the matrix in shared memory, rotations applied
+//           column-wise then row-wise each round (16 disjoint pairs per round).
+// n  > 32 : blocked Jacobi.  Indices are cut into 16-wide blocks; a tournament
+//           pairs the blocks; each pair's 32 x 32 sub-problem is diagonalised by
+//           one warp (the n <= 32 solver), and the resulting 32 x 32 unitaries are
+//           applied to the whole matrix (tile updates Q_P^H H_{PP'} Q_P') and to
+//           the accumulated eigenvectors.  Sweeps repeat until no pair needs a
+//           rotation.
+// Rotation rule for a pair (p, q) with entries a = H_pp, c = H_qq, b = H_pq:
+// rotate iff |b| > tol * max(sqrt(|a c|), floor) with tol = 8 eps and floor =
+// ||H||_F.  As sqrt(|a c|) <= ||H||_F this is a normwise criterion: the sweep stops
+// when every off-diagonal entry is below 8 eps ||H||_F, so eigenvalues carry an
+// absolute error of order eps ||H|| (rounding noise of the tile updates cannot
+// keep the sweeps alive).
+// The rotation G = [[cs, sn], [-sn e^{-i beta}, cs e^{-i beta}]], b = |b| e^{i beta},
+// with t = sign(z) / (|z| + sqrt(1 + z^2)), z = (c - a) / (2 |b|), zeroes b.
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace mpsgb {
+
+namespace {
+constexpr int LDS = 33;  // padded leading dimension of 32 x 32 shared tiles
+
+__host__ __device__ __forceinline__ int slot_player(int slot, int r, int nb) {
+  return slot == 0 ? 0 : 1 + (slot - 1 + r) % (nb - 1);
+}
+
+template <typename R> struct Rot { R cs, sn; Cx<R> ph; };
+
+template <typename R> __device__ __forceinline__ R eps_of();
+template <typename R> __device__ __forceinline__ R tol_of() { return (sizeof(R) == 8 ? R(2) : R(8)) * eps_of<R>(); }
+template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+
+template <typename R>
+__device__ __forceinline__ bool jacobi_rot(R a, R c, Cx<R> b, R tol, R floor_, Rot<R>& rt) {
+  R ab = sqrt(abs2(b));
+  R ref = sqrt(fabs(a * c));
+  if (ref < floor_) ref = floor_;
+  if (!(ab > tol * ref)) { rt.cs = 1; rt.sn = 0; rt.ph = cmake<R>(1, 0); return false; }
+  R z = (c - a) / (R(2) * ab);
+  R t;
+  if (fabs(z) > R(1) / (R(16) * eps_of<R>())) t = R(0.5) / z;
+  else t = (z >= 0 ? R(1) : R(-1)) / (fabs(z) + sqrt(z * z + R(1)));
+  R cs = R(1) / sqrt(t * t + R(1));
+  rt.cs = cs;
+  rt.sn = t * cs;
+  rt.ph = cmake<R>(b.x / ab, -b.y / ab);
+  return true;
+}
+
+// Full cyclic Jacobi of the 32 x 32 Hermitian matrix S (shared, ld LDS) by one warp;
+// Q accumulates the rotations (S_in = Q S_out Q^H).  Returns whether any rotation happened.
+template <typename R>
+__device__ bool warp_jacobi(Cx<R>* S, Cx<R>* Q, R tol, R floor_, int max_sweeps, Rot<R>* rots, int* pq) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < 32; ++i) Q[i * LDS + lane] = cmake<R>(i == lane ? R(1) : R(0), R(0));
+  bool any = false;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < 31; ++r) {
+      __syncwarp();
+      if (lane < 16) {
+        int p = slot_player(lane, r, 32), q = slot_player(31 - lane, r, 32);
+        Rot<R> rt;
+        rotated |= jacobi_rot(S[p * LDS + p].x, S[q * LDS + q].x, S[p * LDS + q], tol, floor_, rt) ? 1 : 0;
+        rots[lane] = rt;
+        pq[2 * lane] = p;
+        pq[2 * lane + 1] = q;
+      }
+      __syncwarp();
+      for (int k = 0; k < 16; ++k) {  // columns: S <- S G, Q <- Q G (lane owns a row)
+        Rot<R> rt = rots[k];
+        if (rt.sn == R(0)) continue;
+        int p = pq[2 * k], q = pq[2 * k + 1];
+        Cx<R> x = S[lane * LDS + p], y = S[lane * LDS + q] * rt.ph;
+        S[lane * LDS + p] = rt.cs * x - rt.sn * y;
+        S[lane * LDS + q] = rt.sn * x + rt.cs * y;
+        x = Q[lane * LDS + p]; y = Q[lane * LDS + q] * rt.ph;
+        Q[lane * LDS + p] = rt.cs * x - rt.sn * y;
+        Q[lane * LDS + q] = rt.sn * x + rt.cs * y;
+      }
+      __syncwarp();
+      for (int k = 0; k < 16; ++k) {  // rows: S <- G^H S (lane owns a column)
+        Rot<R> rt = rots[k];
+        if (rt.sn == R(0)) continue;
+        int p = pq[2 * k], q = pq[2 * k + 1];
+        Cx<R> x = S[p * LDS + lane], y = conj(rt.ph) * S[q * LDS + lane];
+        S[p * LDS + lane] = rt.cs * x - rt.sn * y;
+        S[q * LDS + lane] = rt.sn * x + rt.cs * y;
+      }
+      __syncwarp();
+      if (lane < 16 && rots[lane].sn != R(0)) {
+        int p = pq[2 * lane], q = pq[2 * lane + 1];
+        S[p * LDS + q] = cmake<R>(0, 0);
+        S[q * LDS + p] = cmake<R>(0, 0);
+        S[p * LDS + p].y = 0;
+        S[q * LDS + q].y = 0;
+      }
+    }
+    rotated = __any_sync(0xffffffffu, rotated);
+    if (!rotated) break;
+    any = true;
+  }
+  __syncwarp();
+  return any;
+}
+
+// ---- n <= 32: one warp per matrix, solve + sort + write
+template <typename R>
+__global__ void __launch_bounds__(32) eig_small_kernel(int n, const Cx<R>* A, long long lda, long long sA, R* w,
+                                                        long long sw, Cx<R>* V, long long ldv, long long sV,
+                                                        const double* fro) {
+  __shared__ Cx<R> S[32 * LDS];
+  __shared__ Cx<R> Q[32 * LDS];
+  __shared__ Rot<R> rots[16];
+  __shared__ int pq[32];
+  __shared__ R dg[32];
+  const int lane = threadIdx.x;
+  const long long z = blockIdx.x;
+  const Cx<R>* Ap = A + z * sA;
+  for (int i = 0; i < 32; ++i)
+    S[i * LDS + lane] = (i < n && lane < n) ? Ap[i * lda + lane] : cmake<R>(0, 0);
+  __syncwarp();
+  R fl = (R)sqrt(fro[z]);
+  warp_jacobi<R>(S, Q, tol_of<R>(), fl, 40, rots, pq);
+  dg[lane] = S[lane * LDS + lane].x;
+  __syncwarp();
+  if (lane < n) {
+    R d = dg[lane];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (dg[j] > d || (dg[j] == d && j < lane)) ? 1 : 0;
+    w[z * sw + rank] = d;
+    Cx<R>* Vp = V + z * sV;
+    for (int i = 0; i < n; ++i) Vp[i * ldv + rank] = Q[i * LDS + lane];
+  }
+}
+
+// ---- blocked solver kernels
+// Working copies: H (np x np), Vw (np x np), Qs (npairs x 32 x 32) per problem.
+template <typename R>
+__global__ void blk_init_kernel(int n, int np, const Cx<R>* A, long long lda, long long sA, Cx<R>* H, Cx<R>* Vw) {
+  long long tot = (long long)np * np;
+  const long long z = blockIdx.y;
+  const Cx<R>* Ap = A + z * sA;
+  Cx<R>* Hp = H + z * tot;
+  Cx<R>* Vp = Vw + z * tot;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / np), j = (int)(e - (long long)i * np);
+    Hp[e] = (i < n && j < n) ? Ap[i * lda + j] : cmake<R>(0, 0);
+    Vp[e] = cmake<R>(i == j ? R(1) : R(0), R(0));
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32) blk_pair_kernel(int np, int nb, int round, Cx<R>* H, Cx<R>* Qs, int* flag,
+                                                       int* ident, const double* fro) {
+  __shared__ Cx<R> S[32 * LDS];
+  __shared__ Cx<R> Q[32 * LDS];
+  __shared__ Rot<R> rots[16];
+  __shared__ int pq[32];
+  const int lane = threadIdx.x;
+  const int pair = blockIdx.x;
+  const long long z = blockIdx.y;
+  const int I = slot_player(pair, round, nb), J = slot_player(nb - 1 - pair, round, nb);
+  Cx<R>* Hp = H + z * (long long)np * np;
+  // sub-problem indices: 16 of block I then 16 of block J
+  const int gi_lane = lane < 16 ? I * 16 + lane : J * 16 + (lane - 16);
+  for (int i = 0; i < 32; ++i) {
+    int gi = i < 16 ? I * 16 + i : J * 16 + (i - 16);
+    S[i * LDS + lane] = Hp[(long long)gi * np + gi_lane];
+  }
+  __syncwarp();
+  R fl = (R)sqrt(fro[z]);
+  bool any = warp_jacobi<R>(S, Q, tol_of<R>(), fl, 8, rots, pq);
+  Cx<R>* Qp = Qs + (z * (nb / 2) + pair) * 1024;
+  if (any)
+    for (int i = 0; i < 32; ++i) Qp[i * 32 + lane] = Q[i * LDS + lane];
+  if (lane == 0) {
+    ident[z * (nb / 2) + pair] = any ? 0 : 1;
+    if (any) atomicOr(flag + z, 1);
+  }
+}
+
+// One launch applies the round's rotations: work items [0, np2 * np2) are the tiles
+// H_{PP'} <- Q_P^H H_{PP'} Q_P' (P <= P', mirrored for P < P'); the remaining items are
+// 32-row slabs of the eigenvector matrix, Vw[rows, cols(P)] <- Vw[rows, cols(P)] Q_P.
+// Pairs whose rotation is the identity are skipped.
+template <typename R>
+__global__ void __launch_bounds__(256) blk_update_kernel(int np, int nb, int round, Cx<R>* H, Cx<R>* Vw,
+                                                         const Cx<R>* Qs, const int* ident) {
+  const int npairs = nb / 2;
+  const long long z = blockIdx.y;
+  const int item = blockIdx.x;
+  __shared__ Cx<R> T[32 * LDS];
+  __shared__ Cx<R> M[32 * LDS];
+  const int tid = threadIdx.x;
+  const int* id = ident + z * npairs;
+  if (item < npairs * npairs) {
+    const int P = item / npairs, P2 = item - P * npairs;
+    if (P > P2 || (id[P] && id[P2])) return;
+    Cx<R>* Hp = H + z * (long long)np * np;
+    const Cx<R>* QP = Qs + (z * npairs + P) * 1024;
+    const Cx<R>* QP2 = Qs + (z * npairs + P2) * 1024;
+    const int I = slot_player(P, round, nb), J = slot_player(nb - 1 - P, round, nb);
+    const int I2 = slot_player(P2, round, nb), J2 = slot_player(nb - 1 - P2, round, nb);
+    for (int e = tid; e < 1024; e += 256) {
+      int i = e >> 5, j = e & 31;
+      int gi = i < 16 ? I * 16 + i : J * 16 + (i - 16);
+      int gj = j < 16 ? I2 * 16 + j : J2 * 16 + (j - 16);
+      T[i * LDS + j] = Hp[(long long)gi * np + gj];
+      M[i * LDS + j] = id[P2] ? cmake<R>(i == j ? R(1) : R(0), R(0)) : QP2[e];
+    }
+    __syncthreads();
+    Cx<R> x[4];
+    for (int u = 0; u < 4; ++u) {  // X = T Q_P'
+      int e = tid + 256 * u, i = e >> 5, j = e & 31;
+      Cx<R> acc = cmake<R>(0, 0);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) cfma(acc, T[i * LDS + k], M[k * LDS + j]);
+      x[u] = acc;
+    }
+    __syncthreads();
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + 256 * u, i = e >> 5, j = e & 31;
+      T[i * LDS + j] = x[u];
+      M[i * LDS + j] = id[P] ? cmake<R>(i == j ? R(1) : R(0), R(0)) : QP[e];
+    }
+    __syncthreads();
+    for (int u = 0; u < 4; ++u) {  // Y = Q_P^H X
+      int e = tid + 256 * u, i = e >> 5, j = e & 31;
+      Cx<R> acc = cmake<R>(0, 0);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) cfma(acc, conj(M[k * LDS + i]), T[k * LDS + j]);
+      int gi = i < 16 ? I * 16 + i : J * 16 + (i - 16);
+      int gj = j < 16 ? I2 * 16 + j : J2 * 16 + (j - 16);
+      Hp[(long long)gi * np + gj] = acc;
+      if (P != P2) Hp[(long long)gj * np + gi] = conj(acc);
+    }
+  } else {
+    const int v = item - npairs * npairs;
+    const int P = v % npairs, rc = v / npairs;
+    if (id[P]) return;
+    Cx<R>* Vp = Vw + z * (long long)np * np;
+    const Cx<R>* QP = Qs + (z * npairs + P) * 1024;
+    const int I = slot_player(P, round, nb), J = slot_player(nb - 1 - P, round, nb);
+    for (int e = tid; e < 1024; e += 256) {
+      int i = e >> 5, j = e & 31;
+      int gj = j < 16 ? I * 16 + j : J * 16 + (j - 16);
+      T[i * LDS + j] = Vp[(long long)(rc * 32 + i) * np + gj];
+      M[i * LDS + j] = QP[e];
+    }
+    __syncthreads();
+    for (int u = 0; u < 4; ++u) {
+      int e = tid + 256 * u, i = e >> 5, j = e & 31;
+      Cx<R> acc = cmake<R>(0, 0);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) cfma(acc, T[i * LDS + k], M[k * LDS + j]);
+      int gj = j < 16 ? I * 16 + j : J * 16 + (j - 16);
+      Vp[(long long)(rc * 32 + i) * np + gj] = acc;
+    }
+  }
+}
+
+// diagonal -> descending eigenvalues (rank sort, ties by index) and column gather
+template <typename R>
+__global__ void __launch_bounds__(1024) blk_finish_kernel(int n, int np, const Cx<R>* H, const Cx<R>* Vw, R* w,
+                                                          long long sw, Cx<R>* V, long long ldv, long long sV,
+                                                          int* perm_ws) {
+  extern __shared__ unsigned char smem_raw[];
+  R* dg = reinterpret_cast<R*>(smem_raw);
+  const long long z = blockIdx.x;
+  const Cx<R>* Hp = H + z * (long long)np * np;
+  const Cx<R>* Vp = Vw + z * (long long)np * np;
+  int* perm = perm_ws + z * np;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dg[i] = Hp[(long long)i * np + i].x;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    R d = dg[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (dg[j] > d || (dg[j] == d && j < i)) ? 1 : 0;
+    w[z * sw + rank] = d;
+    perm[rank] = i;
+  }
+  __syncthreads();
+  Cx<R>* Vo = V + z * sV;
+  long long tot = (long long)n * n;
+  for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+    int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    Vo[(long long)i * ldv + j] = Vp[(long long)i * np + perm[j]];
+  }
+}
+
+template <typename R>
+__global__ void fro2_kernel(int n, const Cx<R>* A, long long lda, long long sA, double* out) {
+  const long long z = blockIdx.x;
+  const Cx<R>* Ap = A + z * sA;
+  double acc = 0;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    int i = (int)(e / n), j = (int)(e - (long long)i * n);
+    Cx<R> v = Ap[i * lda + j];
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s[i];
+    out[z] = t;
+  }
+}
+
+inline int padded(int n) { return ((n + 31) / 32) * 32; }
+}  // namespace
+
+size_t eigh_workspace_bytes(int n, int batch, int real_bytes) {
+  size_t c = 2 * (size_t)real_bytes;
+  int np = padded(n);
+  size_t b = 0;
+  b += (size_t)batch * np * np * c * 2;           // H, Vw
+  b += (size_t)batch * (np / 32) * 1024 * c;       // Qs
+  b += (size_t)batch * np * sizeof(int);           // perm
+  b += (size_t)batch * (sizeof(int) + sizeof(double)) + 256;  // flags, norms
+  b += (size_t)batch * (np / 32) * sizeof(int) + 256;         // identity flags
+  return b + 1024;
+}
+
+template <typename R>
+int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
+         long long ldv, long long sV, int batch, void* workspace) {
+  if (n <= 0 || batch <= 0) return 0;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
+  double* fro = reinterpret_cast<double*>(take(sizeof(double) * batch));
+  fro2_kernel<R><<<batch, 256, 0, st>>>(n, A, lda, sA, fro);
+  count_launch();
+  if (n <= 32) {
+    kt_begin(KT_EIG_SMALL, st);
+    eig_small_kernel<R><<<batch, 32, 0, st>>>(n, A, lda, sA, w, sw, V, ldv, sV, fro);
+    kt_end(KT_EIG_SMALL, st);
+    count_launch();
+    return 1;
+  }
+  const int np = padded(n), nb = np / 16, npairs = nb / 2;
+  Cx<R>* H = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)batch * np * np));
+  Cx<R>* Vw = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)batch * np * np));
+  Cx<R>* Qs = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)batch * npairs * 1024));
+  int* perm = reinterpret_cast<int*>(take(sizeof(int) * (size_t)batch * np));
+  int* flag = reinterpret_cast<int*>(take(sizeof(int) * batch));
+  int* ident = reinterpret_cast<int*>(take(sizeof(int) * (size_t)batch * npairs));
+  {
+    long long tot = (long long)np * np;
+    dim3 g((unsigned)((tot + 255) / 256 > 4096 ? 4096 : (tot + 255) / 256), batch);
+    blk_init_kernel<R><<<g, 256, 0, st>>>(n, np, A, lda, sA, H, Vw);
+    count_launch();
+  }
+  int sweeps = -1;
+  // pinned host copy of the per-problem "rotated" flags, kept per host thread
+  thread_local int* hflag = nullptr;
+  thread_local int hcap = 0;
+  if (hcap < batch) {
+    if (hflag) cudaFreeHost(hflag);
+    hcap = batch < 64 ? 64 : batch;
+    if (cudaMallocHost(&hflag, sizeof(int) * hcap) != cudaSuccess) { hflag = nullptr; hcap = 0; return -1; }
+  }
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    cudaMemsetAsync(flag, 0, sizeof(int) * batch, st);
+    for (int r = 0; r < nb - 1; ++r) {
+      kt_begin(KT_EIG_PAIR, st);
+      blk_pair_kernel<R><<<dim3(npairs, batch), 32, 0, st>>>(np, nb, r, H, Qs, flag, ident, fro);
+      kt_end(KT_EIG_PAIR, st);
+      kt_begin(KT_EIG_UPDATE, st);
+      blk_update_kernel<R><<<dim3(npairs * npairs + npairs * (np / 32), batch), 256, 0, st>>>(np, nb, r, H, Vw, Qs, ident);
+      kt_end(KT_EIG_UPDATE, st);
+      kt_add_work(KT_EIG_UPDATE, 8.0 * 32768.0 * batch * ((double)npairs * (npairs + 1) + (double)npairs * (np / 32)));
+      count_launch(2);
+    }
+    cudaMemcpyAsync(hflag, flag, sizeof(int) * batch, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    int any = 0;
+    for (int b = 0; b < batch; ++b) any |= hflag[b];
+    if (!any) { sweeps = sweep + 1; break; }
+  }
+  size_t shm = sizeof(R) * (size_t)n;
+  if (shm > 48 * 1024) cudaFuncSetAttribute(blk_finish_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  blk_finish_kernel<R><<<batch, 1024, shm, st>>>(n, np, H, Vw, w, sw, V, ldv, sV, perm);
+  count_launch();
+  return sweeps;
+}
+
+template int eigh<double>(cudaStream_t, int, const z128*, long long, long long, double*, long long, z128*, long long,
+                          long long, int, void*);
+template int eigh<float>(cudaStream_t, int, const c64*, long long, long long, float*, long long, c64*, long long,
+                         long long, int, void*);
+
+}  // namespace mpsgb

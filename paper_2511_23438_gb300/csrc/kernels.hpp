@@ -1,0 +1,71 @@
+// Host-callable wrappers of the library's CUDA kernels (internal API).
+#pragma once
+#include "common.cuh"
+
+namespace mpsgb {
+
+// ---------------------------------------------------------------- GEMM (gemm.cu)
+template <typename R>
+void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B, Cx<R> beta, View<R> C,
+          int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
+
+// ---------------------------------------------------------------- eigensolver (eig.cu)
+// Hermitian eigendecomposition of `batch` n x n matrices (row-major, leading dim
+// lda, batch stride sA, read only).  Eigenvalues go to w (descending, stride sw),
+// eigenvectors to the columns of V (row-major n x n, leading dim ldv, stride sV):
+// A = V diag(w) V^H.  Cyclic parallel Jacobi: a warp-level solver for n <= 32 and a
+// blocked solver (16-wide blocks, 32 x 32 pair problems solved by warps, tile
+// updates of the full matrix) above.  Returns the number of outer sweeps, or -1 if
+// the sweep limit was hit without convergence.
+size_t eigh_workspace_bytes(int n, int batch, int real_bytes);
+template <typename R>
+int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
+         long long ldv, long long sV, int batch, void* workspace);
+
+// ---------------------------------------------------------------- small kernels (local.cu)
+// blk[a, s, b] <- sum_t U[s, t] blk[a, t, b] for a block of shape (l, d, r); U is d x d row-major on device
+template <typename R>
+void apply_phys(cudaStream_t st, Cx<R>* blk, int l, int d, int r, const Cx<R>* U);
+// product state of Eq. initial_state for one block of k qubits: (1, 2^k, 1)
+template <typename R>
+void init_product(cudaStream_t st, Cx<R>* blk, int k, double c, double s);
+// C = alpha * C over a view
+template <typename R>
+void scale_view(cudaStream_t st, int M, int N, Cx<R> alpha, View<R> C, int batch = 1, long long sC = 0);
+// C = a * X + b * Y (element-wise on M x N views; C may alias X or Y element-for-element)
+template <typename R>
+void axpby(cudaStream_t st, int M, int N, Cx<R> a, View<R> X, Cx<R> b, View<R> Y, View<R> C);
+// copy / convert between precisions: dst(i, j) = src(i, j)
+template <typename Rd, typename Rs>
+void copy_view(cudaStream_t st, int M, int N, View<Rs> src, View<Rd> dst);
+// M[:, j] *= s[j]^p  for p in {+1/2, -1/2} (p2 = +1 or -1), columns j < ncol; rows < nrow
+template <typename R>
+void scale_cols_pow(cudaStream_t st, int nrow, int ncol, Cx<R>* M, long long ld, const R* s, int p2);
+// Z = Y1 + w(s) * Y0 over a block-shaped tensor (l, d, r) with w(s) = sum of z over the block's qubits
+// (mode 1), its square (mode 2) or the bit-flip sum X (mode 3, Y1 may be null).
+template <typename R>
+void weighted_phys(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* Y1, const Cx<R>* Y0, Cx<R>* Z,
+                   double coef);
+// sum_ij conj(X_ij) * Y_ij accumulated in FP64 into out[0..1] (re, im) -- device pointer
+template <typename R>
+void dot_fp64(cudaStream_t st, long long n, const Cx<R>* X, const Cx<R>* Y, double* out);
+// diagonal sum of an n x n row-major matrix into out (FP64)
+template <typename R>
+void trace_fp64(cudaStream_t st, int n, const Cx<R>* A, long long lda, double* out);
+// set to identity / zero
+template <typename R>
+void set_identity(cudaStream_t st, int n, Cx<R>* A, long long lda);
+template <typename R>
+void set_zero(cudaStream_t st, long long count, Cx<R>* A);
+// Build the 2r x 2r right environment of an inter-block gate from Y+ and Y- (r x r each):
+//   E = [[Y+ + Y-, e^{-2i phi} Y+ + e^{2i phi} Y-], [h.c., Y+ + Y-]]
+template <typename R>
+void env_from_split_grams(cudaStream_t st, int r, const Cx<R>* Yp, const Cx<R>* Ym, double phi, Cx<R>* E);
+// Assemble [[E00, E01], [E01^H, E00]] (2r x 2r) from two r x r blocks
+template <typename R>
+void env_assemble(cudaStream_t st, int r, const Cx<R>* E00, const Cx<R>* E01, Cx<R>* E);
+// Place two r x r matrices on the diagonal of a 2r x 2r zero matrix
+template <typename R>
+void block_diag2(cudaStream_t st, int r, const Cx<R>* P, const Cx<R>* Q, Cx<R>* G);
+
+}  // namespace mpsgb

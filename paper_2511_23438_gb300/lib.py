@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libmpsgb (include/mpsgb.h); argument marshalling only.
+
+Every compute step runs in the CUDA library.  If the library is missing this
+module raises instead of falling back to anything else.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmpsgb.so")
+
+# enums of include/mpsgb.h
+FP64, SPLIT_TF32X3, SPLIT_BF16X3, FP32 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "split_tf32x3": SPLIT_TF32X3, "split_bf16x3": SPLIT_BF16X3, "fp32": FP32}
+ROUTE_MPO, ROUTE_SWAP = 0, 1
+LAYER_X, LAYER_ZZ = 0, 1
+Z_TOT, Z_TOT2, X_TOT = 0, 1, 2
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEDOUT", -4: "EDEVICE", -5: "ESTATE"}
+
+
+class MpsgbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("chi_max", ctypes.c_int), ("theta", ctypes.c_double),
+                ("prec", ctypes.c_int), ("route", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("J", ctypes.c_double), ("h", ctypes.c_double), ("dt", ctypes.c_double),
+                ("trotter_order", ctypes.c_int)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_lib = None
+
+_SIGS = {
+    "mpsgb_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Allocator), ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_void_p)]),
+    "mpsgb_apply_layer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "mpsgb_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int]),
+    "mpsgb_truncate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mpsgb_expect": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_observables": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_fidelity": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_singular_values": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "mpsgb_bond_dims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "mpsgb_footprint_bytes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
+    "mpsgb_batch_step": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mpsgb_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "mpsgb_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(Allocator), ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_void_p)]),
+    "mpsgb_destroy": (None, [ctypes.c_void_p]),
+    "mpsgb_last_error": (ctypes.c_char_p, []),
+    "mpsgb_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "mpsgb_launch_count": (ctypes.c_ulonglong, []),
+    "mpsgb_schedule_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+    "mpsgb_schedule_gates": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "mpsgb_kernel_timing": (ctypes.c_int, [ctypes.c_int]),
+    "mpsgb_kernel_times": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_kernel_site_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "mpsgb_initial_theta": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "mpsgb_gamma_fit": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mpsgb_rescale": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_double)]),
+}
+
+
+def exported_symbols():
+    """Names declared in include/mpsgb.h that this binding wraps."""
+    return list(_SIGS)
+
+
+def load(path=None):
+    """Load libmpsgb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libmpsgb.so not found at %s: build it with paper_2511_23438_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise MpsgbError(status, load().mpsgb_last_error().decode())
+
+
+def config(Lx, Ly, chi, theta, prec="fp64", J=-1.0, h=2.0, dt=0.25, order=2, seed=0, route=ROUTE_MPO):
+    return Config(Lx, Ly, chi, theta, PRECISIONS[prec] if isinstance(prec, str) else prec, route, seed, J, h, dt, order)
+
+
+def torch_allocator():
+    """An mpsgb_allocator backed by PyTorch's caching allocator (keep the returned object alive)."""
+    import torch
+
+    def _alloc(size, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
+    a._keep = (_alloc, _free)
+    return a
+
+
+def initial_theta(J, h, dtheta):
+    return load().mpsgb_initial_theta(J, h, dtheta)
+
+
+def gamma_fit(temperature, chi, n):
+    return load().mpsgb_gamma_fit(temperature, chi, n)
+
+
+def rescale(z, z2, F, gamma):
+    out = (ctypes.c_double * 2)()
+    _check(load().mpsgb_rescale(z, z2, F, gamma, out))
+    return out[0], out[1]
+
+
+def schedule_info(Lx, Ly):
+    out = (ctypes.c_longlong * 6)()
+    _check(load().mpsgb_schedule_info(Lx, Ly, out))
+    keys = ("blocks", "zz_bonds", "intra", "inter", "truncations", "dmax")
+    return dict(zip(keys, list(out)))
+
+
+def schedule_gates(Lx, Ly):
+    n = ctypes.c_int()
+    _check(load().mpsgb_schedule_gates(Lx, Ly, None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_int * (6 * n.value))()
+    _check(load().mpsgb_schedule_gates(Lx, Ly, buf, n.value, ctypes.byref(n)))
+    v = list(buf)
+    return [tuple(v[6 * i: 6 * i + 6]) for i in range(n.value)]
+
+
+def footprint_bytes(cfg):
+    b = ctypes.c_size_t()
+    _check(load().mpsgb_footprint_bytes(ctypes.byref(cfg), ctypes.byref(b)))
+    return b.value
+
+
+def launch_count():
+    return load().mpsgb_launch_count()
+
+
+KERNEL_SITES = 7
+
+
+def kernel_timing(enable):
+    _check(load().mpsgb_kernel_timing(1 if enable else 0))
+
+
+def kernel_times():
+    """{site name: (device ms, launches, work)} for every launch site."""
+    out = {}
+    for s in range(KERNEL_SITES):
+        ms, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        _check(load().mpsgb_kernel_times(s, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+        out[load().mpsgb_kernel_site_name(s).decode()] = (ms.value, n.value, w.value)
+    return out
+
+
+class MPS:
+    """One device-resident MPS (an mpsgb handle)."""
+
+    def __init__(self, cfg, stream=None, allocator=None, _handle=None):
+        self.cfg = cfg
+        self._alloc = allocator
+        if _handle is not None:
+            self.h = _handle
+            return
+        h = ctypes.c_void_p()
+        _check(load().mpsgb_create(ctypes.byref(cfg), ctypes.byref(allocator) if allocator else None,
+                                   ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        self.h = h
+
+    @classmethod
+    def load_checkpoint(cls, path, stream=None, allocator=None):
+        h = ctypes.c_void_p()
+        _check(load().mpsgb_load(path.encode(), ctypes.byref(allocator) if allocator else None,
+                                 ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+        return cls(None, _handle=h, allocator=allocator)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mpsgb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_layer(self, layer, angle):
+        _check(load().mpsgb_apply_layer(self.h, layer, angle))
+
+    def step(self, J, h, dt, order=2, nsteps=1):
+        _check(load().mpsgb_step(self.h, J, h, dt, order, nsteps))
+
+    def truncate(self, chi):
+        _check(load().mpsgb_truncate(self.h, chi))
+
+    def observables(self):
+        out = (ctypes.c_double * 4)()
+        _check(load().mpsgb_observables(self.h, out))
+        return {"Z": out[0], "Z2": out[1], "X": out[2], "norm": out[3]}
+
+    def expect(self, obs):
+        v = ctypes.c_double()
+        _check(load().mpsgb_expect(self.h, obs, ctypes.byref(v)))
+        return v.value
+
+    def fidelity(self):
+        v = ctypes.c_double()
+        _check(load().mpsgb_fidelity(self.h, ctypes.byref(v)))
+        return v.value
+
+    def singular_values(self, bond):
+        n = ctypes.c_int()
+        _check(load().mpsgb_singular_values(self.h, bond, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_double * max(1, n.value))()
+        _check(load().mpsgb_singular_values(self.h, bond, buf, n.value, ctypes.byref(n)))
+        return list(buf)[: n.value]
+
+    def bond_dims(self):
+        n = ctypes.c_int()
+        _check(load().mpsgb_bond_dims(self.h, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_int * max(1, n.value))()
+        _check(load().mpsgb_bond_dims(self.h, buf, n.value, ctypes.byref(n)))
+        return list(buf)[: n.value]
+
+    def stats(self):
+        out = (ctypes.c_longlong * 5)()
+        _check(load().mpsgb_stats(self.h, out))
+        return dict(zip(("truncations", "gates", "centre_moves", "eig_calls", "eig_sweeps"), list(out)))
+
+    def save(self, path):
+        _check(load().mpsgb_save(self.h, path.encode()))
+
+
+def batch_step(mps_list, nsteps, flags=0):
+    arr = (ctypes.c_void_p * len(mps_list))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
+                                              for m in mps_list])
+    _check(load().mpsgb_batch_step(arr, len(mps_list), nsteps, flags))

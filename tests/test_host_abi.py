@@ -1,0 +1,80 @@
+"""C ABI and host logic, without a GPU: the library loads, exports every symbol the
+header declares, and its host-only functions agree with the oracle's independent
+layout / schedule and with the paper's gamma table."""
+import json
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from oracle import layout, model, rescale
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mpsgb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_23438_gb300 import build, lib as L
+    build.build()
+    L.load()
+    return L
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpsgb_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    so = lib.load()
+    for n in names:
+        assert hasattr(so, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (mpsgb_\w+)", out))
+    assert set(names) <= exported
+    assert set(lib.exported_symbols()) == set(names)
+
+
+@pytest.mark.parametrize("grid", [(3, 3), (3, 4), (4, 4), (5, 6), (6, 6), (6, 8), (7, 8)])
+def test_schedule_matches_oracle(lib, grid):
+    info = lib.schedule_info(*grid)
+    nb, nintra, dist, ntr = layout.census(*grid)
+    assert info["zz_bonds"] == nb and info["intra"] == nintra and info["truncations"] == ntr
+    assert info["blocks"] == 2 * grid[0]
+    _, inter = layout.schedule(*grid)
+    assert lib.schedule_gates(*grid) == [tuple(g) for g in inter]
+
+
+def test_host_formulas(lib):
+    assert abs(lib.initial_theta(-1.0, 2.0, 0.0) - model.theta_min()) < 1e-15
+    for t, name in enumerate(("low", "mid", "high")):
+        for chi, n in [(64, 30), (1024, 48), (4096, 56)]:
+            assert abs(lib.gamma_fit(t, chi, n) - rescale.gamma_fit(name, chi, n)) < 1e-15
+    assert math.isnan(lib.gamma_fit(3, 64, 30))
+    z, z2 = lib.rescale(0.3, 0.2, 0.5, 0.7)
+    assert abs(z - rescale.rescale_z(0.3, 0.5)) < 1e-16
+    assert abs(z2 - rescale.rescale_z2(0.2, 0.5, 0.7)) < 1e-16
+
+
+def test_footprint(lib):
+    # chi^2 * dmax * blocks * element size (complex128 in the FP64 form)
+    assert lib.footprint_bytes(lib.config(6, 8, 1024, 0.1)) == 1024 ** 2 * 16 * 12 * 16
+    assert lib.footprint_bytes(lib.config(6, 8, 1024, 0.1, prec="fp32")) == 1024 ** 2 * 16 * 12 * 8
+    # chi above every bond bound is capped by the largest bound (3x4: 64)
+    assert lib.footprint_bytes(lib.config(3, 4, 1000, 0.1)) == 64 ** 2 * 4 * 6 * 16
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    for cfg in [lib.config(1, 4, 16, 0.1), lib.config(3, 4, 0, 0.1), lib.config(3, 4, 16, float("nan")),
+                lib.config(3, 4, 16, 0.1, prec=7), lib.config(3, 40, 16, 0.1)]:
+        with pytest.raises(lib.MpsgbError) as e:
+            lib.MPS(cfg)
+        assert e.value.status == -1
+    with pytest.raises(lib.MpsgbError):
+        lib.schedule_info(2, 1)

@@ -305,3 +305,16 @@ def test_rescaling_limits():
     assert rescale.rescale_z(0.3, 1.0) == 0.3
     assert rescale.rescale_z2(0.2, 1.0, 0.7) == 0.2
     assert abs(rescale.rescale_z2(0.2, 0.5, 1.0) - 0.1) < 1e-16
+
+
+def test_per_qubit_initial_angles():
+    # Eq. initial_state with one angle per qubit: <Z_j> = cos(theta_j), <X_j> = sin(theta_j)
+    rng = np.random.default_rng(3)
+    th = rng.uniform(-1, 1, 12)
+    m = mps.MPS(3, 4, 4, th)
+    v = m.to_statevector()
+    assert np.allclose(v, sv.product_state(12, th), atol=1e-15)
+    z, z2, x, _ = m.observables()
+    assert abs(z - np.mean(np.cos(th))) < 1e-14 and abs(x - np.mean(np.sin(th))) < 1e-14
+    zz = (np.sum(np.cos(th)) ** 2 - np.sum(np.cos(th) ** 2) + 12) / 144
+    assert abs(z2 - zz) < 1e-14
