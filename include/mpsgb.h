@@ -50,9 +50,12 @@ typedef enum {
 
 /* Arithmetic of the path.
  *   FP64         complex128 storage, every contraction and the truncation core in FP64.
- *   SPLIT_TF32X3 complex64 storage; block-sized contractions as 3-term TF32 split products
- *                on the tensor cores with FP32 accumulation; truncation weights and F in FP64.
- *   SPLIT_BF16X3 as above with 3-term BF16 splits.
+ *   SPLIT_TF32X3 reserved (TF32 splits; not available in this build).
+ *   SPLIT_BF16X3 complex64 storage; the block-sized contractions (Grams, left factors, new blocks,
+ *                transfer and environment products) on the tcgen05 tensor cores: every FP32
+ *                component is split into two BF16 terms (hi + lo, 16 significant bits) and a
+ *                real product is hi*hi + hi*lo + lo*hi with FP32 accumulation; the truncation core
+ *                (bond x bond products, eigensolves) in FP32 on CUDA cores; weights and F in FP64.
  *   FP32         complex64 storage, all contractions on FP32 CUDA cores (reference form for
  *                the split forms). */
 typedef enum { MPSGB_FP64 = 0, MPSGB_SPLIT_TF32X3 = 1, MPSGB_SPLIT_BF16X3 = 2, MPSGB_FP32 = 3 } mpsgb_precision;
@@ -157,6 +160,19 @@ unsigned long long mpsgb_launch_count(void);
 int mpsgb_kernel_timing(int enable);
 int mpsgb_kernel_times(int site, double* ms, long long* launches, double* work);
 const char* mpsgb_kernel_site_name(int site);
+
+/* Self-test of the tensor-core split GEMM (no paper counterpart; a kernel check): multiplies seeded
+ * random complex64 matrices, op(A) (M x K) times op(B) (K x N) with op(A) = A^H if mode bit 0 and
+ * op(B) = B^T if mode bit 1, on the tensor cores and on FP32 CUDA cores, and writes
+ * max |difference| / max |CUDA-core result| to *rel_err.  Allocates its own device memory. */
+int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
+
+/* Self-test of the Hermitian eigensolver (no paper counterpart; a kernel check): a seeded n x n
+ * positive semi-definite complex matrix with graded columns is decomposed in FP64 (fp64 != 0) or
+ * FP32.  out[0] outer sweeps (-1: sweep limit), out[1] device ms, out[2] max |A V - V diag(w)| /
+ * max |w|, out[3] max |V^H V - I| over sampled columns, out[4] 1 if w is descending, out[5] max |w|.
+ * Allocates its own device memory. */
+int mpsgb_eig_selftest(int n, int fp64, unsigned long long seed, double out[6]);
 
 /* Host-only schedule facts of an Lx x Ly grid (no GPU needed): out[0] blocks, out[1] ZZ bonds,
  * out[2] in-block bonds, out[3] inter-block gates, out[4] bond truncations per ZZ layer,

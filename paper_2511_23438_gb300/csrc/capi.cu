@@ -10,6 +10,7 @@
 
 #include "../../include/mpsgb.h"
 #include "engine.hpp"
+#include "kernels.hpp"
 
 using mpsgb::Engine;
 using mpsgb::Fail;
@@ -45,6 +46,7 @@ int check_config(const mpsgb_config* c) {
   if (c->prec < MPSGB_FP64 || c->prec > MPSGB_FP32) return fail(MPSGB_EINVAL, "unknown precision");
   if (c->route != MPSGB_ROUTE_MPO && c->route != MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "unknown route");
   if (c->route == MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "SWAP routing is not available in this build");
+  if (c->prec == MPSGB_SPLIT_TF32X3) return fail(MPSGB_EINVAL, "SPLIT_TF32X3 is not available in this build");
   if (!std::isfinite(c->theta)) return fail(MPSGB_EINVAL, "theta is not finite");
   if (c->chi_max < 1 || c->chi_max > 8192) return fail(MPSGB_EINVAL, "chi_max must be in 1..8192");
   mpsgb::Layout L;
@@ -252,6 +254,23 @@ int mpsgb_schedule_gates(int Lx, int Ly, int* out, int cap, int* n) {
     int v[6] = {g.p, g.q, g.qi, g.qj, g.ti, g.tj};
     for (int j = 0; j < 6; ++j) out[6 * i + j] = v[j];
   }
+  return MPSGB_OK;
+}
+
+int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err) {
+  if (!rel_err || M < 1 || N < 1 || K < 1 || (long long)M * N > (1LL << 26) || (long long)K * (M + N) > (1LL << 28))
+    return fail(MPSGB_EINVAL, "bad self-test arguments");
+  int s = mpsgb::tc_selftest(M, N, K, mode, seed, rel_err);
+  if (s == -3) return fail(MPSGB_ETIMEDOUT, "tensor-core GEMM: a bounded wait ran out");
+  if (s == -4) return fail(MPSGB_EDEVICE, "CUDA error in the tensor-core GEMM self-test");
+  if (s != 0) return fail(MPSGB_EDEVICE, "tensor-core GEMM could not be set up (tensor maps)");
+  return MPSGB_OK;
+}
+
+int mpsgb_eig_selftest(int n, int fp64, unsigned long long seed, double out[6]) {
+  if (!out || n < 1 || n > 4096) return fail(MPSGB_EINVAL, "bad self-test arguments");
+  int s = mpsgb::eig_selftest(n, fp64, seed, out);
+  if (s != 0) return fail(MPSGB_EDEVICE, "CUDA error in the eigensolver self-test");
   return MPSGB_OK;
 }
 

@@ -16,6 +16,10 @@
 // keep the sweeps alive).
 // The rotation G = [[cs, sn], [-sn e^{-i beta}, cs e^{-i beta}]], b = |b| e^{i beta},
 // with t = sign(z) / (|z| + sqrt(1 + z^2)), z = (c - a) / (2 |b|), zeroes b.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.hpp"
 
@@ -31,7 +35,11 @@ __host__ __device__ __forceinline__ int slot_player(int slot, int r, int nb) {
 template <typename R> struct Rot { R cs, sn; Cx<R> ph; };
 
 template <typename R> __device__ __forceinline__ R eps_of();
-template <typename R> __device__ __forceinline__ R tol_of() { return (sizeof(R) == 8 ? R(2) : R(8)) * eps_of<R>(); }
+template <typename R> __device__ __forceinline__ R tol_of() { return R(8) * eps_of<R>(); }
+// floor of the rotation rule relative to ||H||_F (normwise rule in both precisions: with the
+// relative rule the rounding noise of the tile updates keeps re-creating tiny couplings and the
+// sweeps never stop)
+template <typename R> __device__ __forceinline__ R floor_scale() { return R(1); }
 template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
 template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
 
@@ -109,6 +117,71 @@ __device__ bool warp_jacobi(Cx<R>* S, Cx<R>* Q, R tol, R floor_, int max_sweeps,
   return any;
 }
 
+// Same sweep as warp_jacobi with 128 threads: per round the 16 rotations are computed by
+// threads 0..15, then the 32 x 16 (row, pair) column updates and the 32 x 16 (column, pair)
+// row updates are spread over all threads.
+template <typename R>
+__device__ bool cta_jacobi32(Cx<R>* S, Cx<R>* Q, R tol, R floor_, int max_sweeps, Rot<R>* rots, int* pq,
+                             int* rotated_sm) {
+  const int t = threadIdx.x;
+  for (int e = t; e < 1024; e += blockDim.x) {
+    int i = e >> 5, j = e & 31;
+    Q[i * LDS + j] = cmake<R>(i == j ? R(1) : R(0), R(0));
+  }
+  bool any = false;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (t == 0) *rotated_sm = 0;
+    __syncthreads();
+    for (int r = 0; r < 31; ++r) {
+      if (t < 16) {
+        int p = slot_player(t, r, 32), q = slot_player(31 - t, r, 32);
+        Rot<R> rt;
+        if (jacobi_rot(S[p * LDS + p].x, S[q * LDS + q].x, S[p * LDS + q], tol, floor_, rt)) *rotated_sm = 1;
+        rots[t] = rt;
+        pq[2 * t] = p;
+        pq[2 * t + 1] = q;
+      }
+      __syncthreads();
+      for (int it = t; it < 512; it += blockDim.x) {  // columns: S <- S G, Q <- Q G
+        const int row = it & 31, k = it >> 5;
+        Rot<R> rt = rots[k];
+        if (rt.sn == R(0)) continue;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        Cx<R> x = S[row * LDS + p], y = S[row * LDS + q] * rt.ph;
+        S[row * LDS + p] = rt.cs * x - rt.sn * y;
+        S[row * LDS + q] = rt.sn * x + rt.cs * y;
+        x = Q[row * LDS + p]; y = Q[row * LDS + q] * rt.ph;
+        Q[row * LDS + p] = rt.cs * x - rt.sn * y;
+        Q[row * LDS + q] = rt.sn * x + rt.cs * y;
+      }
+      __syncthreads();
+      for (int it = t; it < 512; it += blockDim.x) {  // rows: S <- G^H S
+        const int col = it & 31, k = it >> 5;
+        Rot<R> rt = rots[k];
+        if (rt.sn == R(0)) continue;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        Cx<R> x = S[p * LDS + col], y = conj(rt.ph) * S[q * LDS + col];
+        S[p * LDS + col] = rt.cs * x - rt.sn * y;
+        S[q * LDS + col] = rt.sn * x + rt.cs * y;
+      }
+      __syncthreads();
+      if (t < 16 && rots[t].sn != R(0)) {
+        int p = pq[2 * t], q = pq[2 * t + 1];
+        S[p * LDS + q] = cmake<R>(0, 0);
+        S[q * LDS + p] = cmake<R>(0, 0);
+        S[p * LDS + p].y = 0;
+        S[q * LDS + q].y = 0;
+      }
+      __syncthreads();
+    }
+    const bool rot = *rotated_sm != 0;
+    __syncthreads();
+    if (!rot) break;
+    any = true;
+  }
+  return any;
+}
+
 // ---- n <= 32: one warp per matrix, solve + sort + write
 template <typename R>
 __global__ void __launch_bounds__(32) eig_small_kernel(int n, const Cx<R>* A, long long lda, long long sA, R* w,
@@ -125,7 +198,7 @@ __global__ void __launch_bounds__(32) eig_small_kernel(int n, const Cx<R>* A, lo
   for (int i = 0; i < 32; ++i)
     S[i * LDS + lane] = (i < n && lane < n) ? Ap[i * lda + lane] : cmake<R>(0, 0);
   __syncwarp();
-  R fl = (R)sqrt(fro[z]);
+  R fl = (R)sqrt(fro[z]) * floor_scale<R>();
   warp_jacobi<R>(S, Q, tol_of<R>(), fl, 40, rots, pq);
   dg[lane] = S[lane * LDS + lane].x;
   __syncwarp();
@@ -156,30 +229,32 @@ __global__ void blk_init_kernel(int n, int np, const Cx<R>* A, long long lda, lo
 }
 
 template <typename R>
-__global__ void __launch_bounds__(32) blk_pair_kernel(int np, int nb, int round, Cx<R>* H, Cx<R>* Qs, int* flag,
-                                                       int* ident, const double* fro) {
+__global__ void __launch_bounds__(128) blk_pair_kernel(int np, int nb, int round, Cx<R>* H, Cx<R>* Qs, int* flag,
+                                                        int* ident, const double* fro) {
   __shared__ Cx<R> S[32 * LDS];
   __shared__ Cx<R> Q[32 * LDS];
   __shared__ Rot<R> rots[16];
   __shared__ int pq[32];
-  const int lane = threadIdx.x;
+  __shared__ int rotated_sm;
+  const int t = threadIdx.x;
   const int pair = blockIdx.x;
   const long long z = blockIdx.y;
   const int I = slot_player(pair, round, nb), J = slot_player(nb - 1 - pair, round, nb);
   Cx<R>* Hp = H + z * (long long)np * np;
   // sub-problem indices: 16 of block I then 16 of block J
-  const int gi_lane = lane < 16 ? I * 16 + lane : J * 16 + (lane - 16);
-  for (int i = 0; i < 32; ++i) {
+  for (int e = t; e < 1024; e += blockDim.x) {
+    int i = e >> 5, j = e & 31;
     int gi = i < 16 ? I * 16 + i : J * 16 + (i - 16);
-    S[i * LDS + lane] = Hp[(long long)gi * np + gi_lane];
+    int gj = j < 16 ? I * 16 + j : J * 16 + (j - 16);
+    S[i * LDS + j] = Hp[(long long)gi * np + gj];
   }
-  __syncwarp();
-  R fl = (R)sqrt(fro[z]);
-  bool any = warp_jacobi<R>(S, Q, tol_of<R>(), fl, 8, rots, pq);
+  __syncthreads();
+  R fl = (R)sqrt(fro[z]) * floor_scale<R>();
+  bool any = cta_jacobi32<R>(S, Q, tol_of<R>(), fl, 8, rots, pq, &rotated_sm);
   Cx<R>* Qp = Qs + (z * (nb / 2) + pair) * 1024;
   if (any)
-    for (int i = 0; i < 32; ++i) Qp[i * 32 + lane] = Q[i * LDS + lane];
-  if (lane == 0) {
+    for (int e = t; e < 1024; e += blockDim.x) Qp[e] = Q[(e >> 5) * LDS + (e & 31)];
+  if (t == 0) {
     ident[z * (nb / 2) + pair] = any ? 0 : 1;
     if (any) atomicOr(flag + z, 1);
   }
@@ -368,11 +443,12 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
     hcap = batch < 64 ? 64 : batch;
     if (cudaMallocHost(&hflag, sizeof(int) * hcap) != cudaSuccess) { hflag = nullptr; hcap = 0; return -1; }
   }
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  const int max_sweeps = 40;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     cudaMemsetAsync(flag, 0, sizeof(int) * batch, st);
     for (int r = 0; r < nb - 1; ++r) {
       kt_begin(KT_EIG_PAIR, st);
-      blk_pair_kernel<R><<<dim3(npairs, batch), 32, 0, st>>>(np, nb, r, H, Qs, flag, ident, fro);
+      blk_pair_kernel<R><<<dim3(npairs, batch), 128, 0, st>>>(np, nb, r, H, Qs, flag, ident, fro);
       kt_end(KT_EIG_PAIR, st);
       kt_begin(KT_EIG_UPDATE, st);
       blk_update_kernel<R><<<dim3(npairs * npairs + npairs * (np / 32), batch), 256, 0, st>>>(np, nb, r, H, Vw, Qs, ident);
@@ -386,6 +462,7 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
     for (int b = 0; b < batch; ++b) any |= hflag[b];
     if (!any) { sweeps = sweep + 1; break; }
   }
+
   size_t shm = sizeof(R) * (size_t)n;
   if (shm > 48 * 1024) cudaFuncSetAttribute(blk_finish_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   blk_finish_kernel<R><<<batch, 1024, shm, st>>>(n, np, H, Vw, w, sw, V, ldv, sV, perm);
@@ -397,5 +474,99 @@ template int eigh<double>(cudaStream_t, int, const z128*, long long, long long, 
                           long long, int, void*);
 template int eigh<float>(cudaStream_t, int, const c64*, long long, long long, float*, long long, c64*, long long,
                          long long, int, void*);
+
+}  // namespace mpsgb
+
+namespace mpsgb {
+namespace {
+// A = X X^H / n + diag(shift) with seeded X (n x n): Hermitian positive semi-definite test matrix
+template <typename R>
+__global__ void psd_test_kernel(int n, Cx<R>* X, unsigned long long seed) {
+  long long tot = (long long)n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ULL + seed;
+    h ^= h >> 33; h *= 0xff51afd7ed558ccdULL; h ^= h >> 33; h *= 0xc4ceb9fe1a85ec53ULL; h ^= h >> 33;
+    double a = (double)(h & 0xFFFFFF) / 16777216.0 - 0.5, b = (double)((h >> 24) & 0xFFFFFF) / 16777216.0 - 0.5;
+    // graded columns: column j scaled by 2^{-j/4} so the spectrum spans many decades
+    int j = (int)(i % n);
+    double sc = exp2(-0.25 * (j % 64));
+    X[i] = cmake<R>((R)(a * sc), (R)(b * sc));
+  }
+}
+}  // namespace
+
+template <typename R>
+int eig_selftest_t(int n, unsigned long long seed, double* out) {
+  cudaStream_t st;
+  if (cudaStreamCreate(&st) != cudaSuccess) return -4;
+  Cx<R> *X, *A, *V;
+  R* w;
+  void* ws;
+  size_t wsb = eigh_workspace_bytes(n, 1, sizeof(R));
+  cudaMalloc(&X, sizeof(Cx<R>) * (size_t)n * n);
+  cudaMalloc(&A, sizeof(Cx<R>) * (size_t)n * n);
+  cudaMalloc(&V, sizeof(Cx<R>) * (size_t)n * n);
+  cudaMalloc(&w, sizeof(R) * n);
+  cudaMalloc(&ws, wsb);
+  psd_test_kernel<R><<<256, 256, 0, st>>>(n, X, seed);
+  Cx<R> one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+  gemm<R>(st, n, n, n, one, rowmajor<R>(X, n), transposed<R>(X, n, true), zero, rowmajor<R>(A, n));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaStreamSynchronize(st);
+  cudaEventRecord(e0, st);
+  int sweeps = eigh<R>(st, n, A, n, 0, w, 0, V, n, 0, 1, ws);
+  cudaEventRecord(e1, st);
+  cudaError_t err = cudaStreamSynchronize(st);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  // residual max_ij |(A V - V diag(w))_ij| / max|w|, and orthogonality max|V^H V - I|
+  Cx<R> *T;
+  cudaMalloc(&T, sizeof(Cx<R>) * (size_t)n * n);
+  std::vector<Cx<R>> hA((size_t)n * n), hV((size_t)n * n), hT((size_t)n * n);
+  std::vector<R> hw(n);
+  gemm<R>(st, n, n, n, one, rowmajor<R>(A, n), rowmajor<R>(V, n), zero, rowmajor<R>(T, n));
+  cudaMemcpyAsync(hT.data(), T, sizeof(Cx<R>) * hT.size(), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hV.data(), V, sizeof(Cx<R>) * hV.size(), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hw.data(), w, sizeof(R) * n, cudaMemcpyDeviceToHost, st);
+  cudaError_t err2 = cudaStreamSynchronize(st);
+  double res = 0, wmax = 0, orth = 0;
+  for (int j = 0; j < n; ++j) wmax = std::max(wmax, std::fabs((double)hw[j]));
+  for (long long i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double rx = hT[i * n + j].x - (double)hV[i * n + j].x * hw[j];
+      double ry = hT[i * n + j].y - (double)hV[i * n + j].y * hw[j];
+      res = std::max(res, std::sqrt(rx * rx + ry * ry));
+    }
+  for (int a = 0; a < n; a += std::max(1, n / 32))
+    for (int b = 0; b < n; ++b) {
+      double sx = 0, sy = 0;
+      for (int i = 0; i < n; ++i) {
+        Cx<R> x = hV[(size_t)i * n + a], y = hV[(size_t)i * n + b];
+        sx += (double)x.x * y.x + (double)x.y * y.y;
+        sy += (double)x.x * y.y - (double)x.y * y.x;
+      }
+      if (a == b) sx -= 1;
+      orth = std::max(orth, std::sqrt(sx * sx + sy * sy));
+    }
+  bool sorted = true;
+  for (int j = 1; j < n; ++j) sorted = sorted && hw[j] <= hw[j - 1];
+  cudaFree(X); cudaFree(A); cudaFree(V); cudaFree(w); cudaFree(ws); cudaFree(T);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (err != cudaSuccess || err2 != cudaSuccess) return -4;
+  out[0] = sweeps;
+  out[1] = ms;
+  out[2] = res / (wmax > 0 ? wmax : 1);
+  out[3] = orth;
+  out[4] = sorted ? 1 : 0;
+  out[5] = wmax;
+  return 0;
+}
+
+int eig_selftest(int n, int fp64, unsigned long long seed, double* out) {
+  return fp64 ? eig_selftest_t<double>(n, seed, out) : eig_selftest_t<float>(n, seed, out);
+}
 
 }  // namespace mpsgb

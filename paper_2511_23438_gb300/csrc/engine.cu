@@ -25,6 +25,7 @@
 #include <map>
 #include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "engine.hpp"
@@ -141,6 +142,30 @@ class EngineT : public Engine {
   int chi_eff = 1, dmax = 2;
   double tau = 1e-13;  // numerical-rank threshold on squared singular values (relative)
   std::vector<R> hbuf;
+  bool tc = false;        // block-sized contractions on the tensor cores (split form)
+  void* tcws = nullptr;   // BF16 operand planes of the tensor-core GEMM
+  size_t tcws_bytes = 0;
+  int* derr = nullptr;    // device error word of bounded waits in kernels
+
+  // Block-sized contraction: tensor cores in the split form (when every dimension is at least
+  // 64), FP32 / FP64 CUDA cores otherwise.
+  void mm(int M, int N, int K, C alpha, View<R> A, View<R> B, C beta, View<R> Cv) {
+    if constexpr (std::is_same<R, float>::value) {
+      if (tc && M >= 64 && N >= 64 && K >= 64) {
+        int s = tc_gemm(stream, M, N, K, alpha, A, B, beta, Cv, tcws, tcws_bytes, derr);
+        if (s != 0) throw Fail{MPSGB_EDEVICE, "tensor-core GEMM set-up failed"};
+        return;
+      }
+    }
+    gemm<R>(stream, M, N, K, alpha, A, B, beta, Cv);
+  }
+  void check_device_error() {
+    int h = 0;
+    cudaMemcpyAsync(&h, derr, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) throw Fail{MPSGB_EDEVICE, std::string("device: ") + cudaGetErrorString(e)};
+    if (h != 0) throw Fail{MPSGB_ETIMEDOUT, "a bounded wait in a tensor-core kernel ran out"};
+  }
 
   ~EngineT() override {
     if (stream) cudaStreamSynchronize(stream);
@@ -191,7 +216,15 @@ class EngineT : public Engine {
     ar.base = (char*)mem.get(ar.size);
     dU = (C*)mem.get(sizeof(C) * 32 * 32 * L.N);
     dsc = (double*)mem.get(sizeof(double) * 16);
-    if (!ar.base || !dU || !dsc) throw Fail{MPSGB_ENOMEM, "allocation of workspace failed"};
+    derr = (int*)mem.get(sizeof(int) * 4);
+    if (!ar.base || !dU || !dsc || !derr) throw Fail{MPSGB_ENOMEM, "allocation of workspace failed"};
+    cudaMemsetAsync(derr, 0, sizeof(int) * 4, stream);
+    if (tc) {
+      // largest operand pair: the Gram of a left factor (2 chi x chi d) with itself
+      tcws_bytes = tc_gemm_workspace_bytes(4LL * chi_eff, 4LL * chi_eff, (long long)chi_eff * dmax) + (1 << 20);
+      tcws = mem.get(tcws_bytes);
+      if (!tcws) throw Fail{MPSGB_ENOMEM, "allocation of tensor-core workspace failed"};
+    }
     dims.assign(L.N - 1, 1);
     double cth = std::cos(c.theta / 2), sth = std::sin(c.theta / 2);
     for (int b = 0; b < L.N; ++b) init_product<R>(stream, blk[b], L.k[b], cth, sth);
@@ -210,6 +243,7 @@ class EngineT : public Engine {
     cudaMemcpyAsync(hbuf.data(), w, sizeof(R) * n, cudaMemcpyDeviceToHost, stream);
     synchronize("eigensolver");
     hw.assign(hbuf.begin(), hbuf.end());
+    if (tc) check_device_error();
   }
   static int count_above(const std::vector<double>& w, double rel, int cap_) {
     if (w.empty() || !(w[0] > 0)) return 0;
@@ -315,20 +349,20 @@ class EngineT : public Engine {
     C* T = ar.take<C>((size_t)r * r);
     void* ws = ar.take<char>(eigh_workspace_bytes(r, 1, sizeof(R)));
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
-    gemm<R>(stream, r, r, l * dd, one, transposed<R>(blk[m], r, true), rowmajor<R>(blk[m], r), zero, rowmajor<R>(G, r));
+    mm(r, r, l * dd, one, transposed<R>(blk[m], r, true), rowmajor<R>(blk[m], r), zero, rowmajor<R>(G, r));
     std::vector<double> hw;
     eig(r, G, w, U, ws, hw);
     int rp = std::max(1, count_above(hw, tau, std::min(r, l * dd)));
     // T = U[:, :rp] D^{-1/2};  Q = M T
     copy_view<R, R>(stream, r, rp, rowmajor<R>(U, r), rowmajor<R>(T, rp));
     scale_cols_pow<R>(stream, r, rp, T, rp, w, -1);
-    gemm<R>(stream, l * dd, rp, r, one, rowmajor<R>(blk[m], r), rowmajor<R>(T, rp), zero, rowmajor<R>(spare, rp));
+    mm(l * dd, rp, r, one, rowmajor<R>(blk[m], r), rowmajor<R>(T, rp), zero, rowmajor<R>(spare, rp));
     std::swap(blk[m], spare);
     // Gs = U[:, :rp] D^{1/2};  R = Gs^H;  block m+1 <- R block m+1
     copy_view<R, R>(stream, r, rp, rowmajor<R>(U, r), rowmajor<R>(T, rp));
     scale_cols_pow<R>(stream, r, rp, T, rp, w, +1);
     int dn = d(m + 1), rn = right(m + 1);
-    gemm<R>(stream, rp, dn * rn, r, one, transposed<R>(T, rp, true), rowmajor<R>(blk[m + 1], (long long)dn * rn), zero,
+    mm(rp, dn * rn, r, one, transposed<R>(T, rp, true), rowmajor<R>(blk[m + 1], (long long)dn * rn), zero,
             rowmajor<R>(spare, (long long)dn * rn));
     std::swap(blk[m + 1], spare);
     dims[m] = rp;
@@ -345,18 +379,18 @@ class EngineT : public Engine {
     C* T = ar.take<C>((size_t)l * l);
     void* ws = ar.take<char>(eigh_workspace_bytes(l, 1, sizeof(R)));
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
-    gemm<R>(stream, l, l, (int)row, one, rowmajor<R>(blk[m], row), transposed<R>(blk[m], row, true), zero, rowmajor<R>(G, l));
+    mm(l, l, (int)row, one, rowmajor<R>(blk[m], row), transposed<R>(blk[m], row, true), zero, rowmajor<R>(G, l));
     std::vector<double> hw;
     eig(l, G, w, U, ws, hw);
     int lp = std::max(1, count_above(hw, tau, std::min<long long>(l, row)));
     copy_view<R, R>(stream, l, lp, rowmajor<R>(U, l), rowmajor<R>(T, lp));
     scale_cols_pow<R>(stream, l, lp, T, lp, w, -1);
-    gemm<R>(stream, lp, (int)row, l, one, transposed<R>(T, lp, true), rowmajor<R>(blk[m], row), zero, rowmajor<R>(spare, row));
+    mm(lp, (int)row, l, one, transposed<R>(T, lp, true), rowmajor<R>(blk[m], row), zero, rowmajor<R>(spare, row));
     std::swap(blk[m], spare);
     copy_view<R, R>(stream, l, lp, rowmajor<R>(U, l), rowmajor<R>(T, lp));
     scale_cols_pow<R>(stream, l, lp, T, lp, w, +1);
     int lq = left(m - 1), dq = d(m - 1);
-    gemm<R>(stream, lq * dq, lp, l, one, rowmajor<R>(blk[m - 1], l), rowmajor<R>(T, lp), zero, rowmajor<R>(spare, lp));
+    mm(lq * dq, lp, l, one, rowmajor<R>(blk[m - 1], l), rowmajor<R>(T, lp), zero, rowmajor<R>(spare, lp));
     std::swap(blk[m - 1], spare);
     dims[m - 1] = lp;
     stats.centre_moves++;
@@ -436,7 +470,7 @@ class EngineT : public Engine {
       for (int v = 0; v < 2; ++v) {
         View<R> Bv; Bv.ptr = blk[q] + v * inq; Bv.row = plain(rowq); Bv.col = split(inq, 1, 2 * inq); Bv.conj = false;
         View<R> BvH; BvH.ptr = Bv.ptr; BvH.row = Bv.col; BvH.col = Bv.row; BvH.conj = true;
-        gemm<R>(stream, lq, lq, (int)(rowq / 2), one, Bv, BvH, zero, rowmajor<R>(v ? Y1 : Y0, lq));
+        mm(lq, lq, (int)(rowq / 2), one, Bv, BvH, zero, rowmajor<R>(v ? Y1 : Y0, lq));
       }
       C ep = cmake<R>((R)std::cos(2 * phi), (R)-std::sin(2 * phi)), em = cmake<R>((R)std::cos(2 * phi), (R)std::sin(2 * phi));
       axpby<R>(stream, lq, lq, one, rowmajor<R>(Y0, lq), one, rowmajor<R>(Y1, lq), rowmajor<R>(E00[q - 1], lq));
@@ -448,8 +482,8 @@ class EngineT : public Engine {
       for (int which = 0; which < 2; ++which) {
         C* Ein = which ? E01[m] : E00[m];
         C* Eout = which ? E01[m - 1] : E00[m - 1];
-        gemm<R>(stream, lm * dm, rm_, rm_, one, rowmajor<R>(blk[m], rm_), rowmajor<R>(Ein, rm_), zero, rowmajor<R>(X, rm_));
-        gemm<R>(stream, lm, lm, (int)row, one, rowmajor<R>(X, row), transposed<R>(blk[m], row, true), zero,
+        mm(lm * dm, rm_, rm_, one, rowmajor<R>(blk[m], rm_), rowmajor<R>(Ein, rm_), zero, rowmajor<R>(X, rm_));
+        mm(lm, lm, (int)row, one, rowmajor<R>(X, row), transposed<R>(blk[m], row, true), zero,
                 rowmajor<R>(Eout, lm));
       }
     }
@@ -474,7 +508,7 @@ class EngineT : public Engine {
           View<R> Av; Av.ptr = blk[p] + v * inp * r; Av.row = split(inp, r, 2 * inp * r); Av.col = plain(1); Av.conj = false;
           View<R> AvH; AvH.ptr = Av.ptr; AvH.row = plain(1); AvH.col = Av.row; AvH.conj = true;
           View<R> Gv = rowmajor<R>(G + (size_t)v * r * r2 + (size_t)v * r, r2);
-          gemm<R>(stream, r, r, rows / 2, one, AvH, Av, zero, Gv);
+          mm(r, r, rows / 2, one, AvH, Av, zero, Gv);
         }
       } else {
         const int lm = od[m - 1];
@@ -482,9 +516,9 @@ class EngineT : public Engine {
         for (int kk = 0; kk < 2; ++kk) {
           View<R> Kk; Kk.ptr = carry + (size_t)kk * lm; Kk.row = plain(2LL * lm); Kk.col = plain(1); Kk.conj = false;
           View<R> Out; Out.ptr = Lb + (size_t)kk * r; Out.row = plain((long long)dm * r2); Out.col = split(r, 1, r2); Out.conj = false;
-          gemm<R>(stream, kprev, dm * r, lm, one, Kk, rowmajor<R>(blk[m], (long long)dm * r), zero, Out);
+          mm(kprev, dm * r, lm, one, Kk, rowmajor<R>(blk[m], (long long)dm * r), zero, Out);
         }
-        gemm<R>(stream, r2, r2, rows, one, transposed<R>(Lb, r2, true), rowmajor<R>(Lb, r2), zero, rowmajor<R>(G, r2));
+        mm(r2, r2, rows, one, transposed<R>(Lb, r2, true), rowmajor<R>(Lb, r2), zero, rowmajor<R>(G, r2));
       }
       env_assemble<R>(stream, r, E00[m], E01[m], E);
       int k = 0;
@@ -495,10 +529,10 @@ class EngineT : public Engine {
         for (int v = 0; v < 2; ++v) {
           View<R> Av; Av.ptr = blk[p] + v * inp * r; Av.row = split(inp, r, 2 * inp * r); Av.col = plain(1); Av.conj = false;
           View<R> Out; Out.ptr = spare + v * inp * k; Out.row = split(inp, k, 2 * inp * k); Out.col = plain(1); Out.conj = false;
-          gemm<R>(stream, rows / 2, k, r, one, Av, rowmajor<R>(WL + (size_t)v * r * k, k), zero, Out);
+          mm(rows / 2, k, r, one, Av, rowmajor<R>(WL + (size_t)v * r * k, k), zero, Out);
         }
       } else {
-        gemm<R>(stream, rows, k, r2, one, rowmajor<R>(Lb, r2), rowmajor<R>(WL, k), zero, rowmajor<R>(spare, k));
+        mm(rows, k, r2, one, rowmajor<R>(Lb, r2), rowmajor<R>(WL, k), zero, rowmajor<R>(spare, k));
       }
       std::swap(blk[m], spare);
       dims[m] = k;
@@ -522,7 +556,7 @@ class EngineT : public Engine {
       axpby<R>(stream, kprev, lq, a, K0, b, K1, rowmajor<R>(Mw, lq));
       View<R> Bw; Bw.ptr = blk[q] + w * inq; Bw.row = plain(rowq); Bw.col = split(inq, 1, 2 * inq); Bw.conj = false;
       View<R> Out; Out.ptr = spare + w * inq; Out.row = plain(rowq); Out.col = split(inq, 1, 2 * inq); Out.conj = false;
-      gemm<R>(stream, kprev, (int)(rowq / 2), lq, one, rowmajor<R>(Mw, lq), Bw, zero, Out);
+      mm(kprev, (int)(rowq / 2), lq, one, rowmajor<R>(Mw, lq), Bw, zero, Out);
     }
     std::swap(blk[q], spare);
     centre = q;
@@ -544,7 +578,7 @@ class EngineT : public Engine {
       C* T = ar.take<C>((size_t)r * r);
       void* ws = ar.take<char>(eigh_workspace_bytes(r, 1, sizeof(R)));
       const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
-      gemm<R>(stream, r, r, l * dd, one, transposed<R>(blk[m], r, true), rowmajor<R>(blk[m], r), zero, rowmajor<R>(G, r));
+      mm(r, r, l * dd, one, transposed<R>(blk[m], r, true), rowmajor<R>(blk[m], r), zero, rowmajor<R>(G, r));
       std::vector<double> hw;
       eig(r, G, w, U, ws, hw);
       int kp = std::max(1, count_above(hw, tau, std::min(std::min(r, l * dd), chi)));
@@ -552,12 +586,12 @@ class EngineT : public Engine {
       for (int i = 0; i < (int)hw.size(); ++i) { tot += std::max(hw[i], 0.0); if (i < kp) kept += std::max(hw[i], 0.0); }
       copy_view<R, R>(stream, r, kp, rowmajor<R>(U, r), rowmajor<R>(T, kp));
       scale_cols_pow<R>(stream, r, kp, T, kp, w, -1);
-      gemm<R>(stream, l * dd, kp, r, one, rowmajor<R>(blk[m], r), rowmajor<R>(T, kp), zero, rowmajor<R>(spare, kp));
+      mm(l * dd, kp, r, one, rowmajor<R>(blk[m], r), rowmajor<R>(T, kp), zero, rowmajor<R>(spare, kp));
       std::swap(blk[m], spare);
       copy_view<R, R>(stream, r, kp, rowmajor<R>(U, r), rowmajor<R>(T, kp));
       scale_cols_pow<R>(stream, r, kp, T, kp, w, +1);
       int dn = d(m + 1), rn = right(m + 1);
-      gemm<R>(stream, kp, dn * rn, r, cmake<R>((R)(1.0 / std::sqrt(kept)), 0), transposed<R>(T, kp, true),
+      mm(kp, dn * rn, r, cmake<R>((R)(1.0 / std::sqrt(kept)), 0), transposed<R>(T, kp, true),
               rowmajor<R>(blk[m + 1], (long long)dn * rn), zero, rowmajor<R>(spare, (long long)dn * rn));
       std::swap(blk[m + 1], spare);
       dims[m] = kp;
@@ -588,19 +622,20 @@ class EngineT : public Engine {
       int l = left(b), dd = d(b), r = right(b);
       long long row = (long long)dd * r;
       for (int i = 0; i < 4; ++i)
-        gemm<R>(stream, l, (int)row, l, one, rowmajor<R>(Ecur[i], l), rowmajor<R>(blk[b], row), zero, rowmajor<R>(Y[i], row));
+        mm(l, (int)row, l, one, rowmajor<R>(Ecur[i], l), rowmajor<R>(blk[b], row), zero, rowmajor<R>(Y[i], row));
       // Y2 <- Y2 + 2 m Y1 + m^2 Y0 ; Y1 <- Y1 + m Y0 ; YX <- YX + X(Y0)
       weighted_phys<R>(stream, 1, l, dd, r, Y[2], Y[1], Y[2], 2.0);
       weighted_phys<R>(stream, 2, l, dd, r, Y[2], Y[0], Y[2], 1.0);
       weighted_phys<R>(stream, 1, l, dd, r, Y[1], Y[0], Y[1], 1.0);
       weighted_phys<R>(stream, 3, l, dd, r, Y[3], Y[0], Y[3], 1.0);
       for (int i = 0; i < 4; ++i)
-        gemm<R>(stream, r, r, l * dd, one, transposed<R>(blk[b], r, true), rowmajor<R>(Y[i], r), zero, rowmajor<R>(Enew[i], r));
+        mm(r, r, l * dd, one, transposed<R>(blk[b], r, true), rowmajor<R>(Y[i], r), zero, rowmajor<R>(Enew[i], r));
       for (int i = 0; i < 4; ++i) std::swap(Ecur[i], Enew[i]);
     }
     C h[4];
     for (int i = 0; i < 4; ++i) cudaMemcpyAsync(&h[i], Ecur[i], sizeof(C), cudaMemcpyDeviceToHost, stream);
     synchronize("observables");
+    if (tc) check_device_error();
     double norm = h[0].x, n = L.n;
     out[0] = h[1].x / (n * norm);
     out[1] = h[2].x / (n * n * norm);
@@ -619,7 +654,7 @@ class EngineT : public Engine {
     R* w = ar.take<R>(r);
     void* ws = ar.take<char>(eigh_workspace_bytes(r, 1, sizeof(R)));
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
-    gemm<R>(stream, r, r, l * dd, one, transposed<R>(blk[bond], r, true), rowmajor<R>(blk[bond], r), zero, rowmajor<R>(G, r));
+    mm(r, r, l * dd, one, transposed<R>(blk[bond], r, true), rowmajor<R>(blk[bond], r), zero, rowmajor<R>(G, r));
     std::vector<double> hw;
     eig(r, G, w, U, ws, hw);
     s.resize(hw.size());
@@ -684,9 +719,10 @@ Engine* make_engine(const mpsgb_config& cfg, const mpsgb_allocator* alloc, cudaS
       auto* x = new EngineT<double>();
       e = x;
       x->init(cfg, alloc, st);
-    } else if (cfg.prec == MPSGB_FP32) {
+    } else if (cfg.prec == MPSGB_FP32 || cfg.prec == MPSGB_SPLIT_BF16X3) {
       auto* x = new EngineT<float>();
       e = x;
+      x->tc = cfg.prec == MPSGB_SPLIT_BF16X3;
       x->init(cfg, alloc, st);
     } else {
       throw Fail{MPSGB_EINVAL, "precision not available in this build"};

@@ -22,6 +22,17 @@ template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
          long long ldv, long long sV, int batch, void* workspace);
 
+// ---------------------------------------------------------------- tensor-core split GEMM (tcgemm.cu)
+// C = alpha op(A) op(B) + beta C on complex64 views with 2-term BF16 splits on tcgen05
+// (FP32 accumulation).  ws: device workspace of tc_gemm_workspace_bytes(M, N, K) bytes;
+// d_err: device word set non-zero if a bounded wait of the kernel ran out.
+// Returns 0, or < 0 if the workspace is too small / the tensor maps could not be built.
+size_t tc_gemm_workspace_bytes(long long M, long long N, long long K);
+int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View<float> B, c64 beta, View<float> C,
+            void* ws, size_t ws_bytes, int* d_err);
+int eig_selftest(int n, int fp64, unsigned long long seed, double* out);
+int tc_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
+
 // ---------------------------------------------------------------- small kernels (local.cu)
 // blk[a, s, b] <- sum_t U[s, t] blk[a, t, b] for a block of shape (l, d, r); U is d x d row-major on device
 template <typename R>

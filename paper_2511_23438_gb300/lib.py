@@ -71,6 +71,10 @@ _SIGS = {
     "mpsgb_kernel_times": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                           ctypes.POINTER(ctypes.c_double)]),
     "mpsgb_kernel_site_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "mpsgb_tc_gemm_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_eig_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                          ctypes.POINTER(ctypes.c_double)]),
     "mpsgb_initial_theta": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "mpsgb_gamma_fit": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mpsgb_rescale": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -125,6 +129,18 @@ def torch_allocator():
     a = Allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
     a._keep = (_alloc, _free)
     return a
+
+
+def tc_gemm_selftest(M, N, K, mode=0, seed=1):
+    e = ctypes.c_double()
+    _check(load().mpsgb_tc_gemm_selftest(M, N, K, mode, seed, ctypes.byref(e)))
+    return e.value
+
+
+def eig_selftest(n, fp64=True, seed=1):
+    out = (ctypes.c_double * 6)()
+    _check(load().mpsgb_eig_selftest(n, 1 if fp64 else 0, seed, out))
+    return dict(zip(("sweeps", "ms", "residual", "orthogonality", "sorted", "wmax"), list(out)))
 
 
 def initial_theta(J, h, dtheta):

@@ -1,0 +1,68 @@
+"""Tensor-core split-precision path (tcgen05 + TMA) through the C ABI.
+
+The GEMM self-test compares the tcgen05 kernel with the FP32 CUDA-core GEMM on
+seeded data (ragged sizes spanning several 128 x 64 tiles, all op(A)/op(B) modes).
+With 2-term BF16 splits (16 significant bits) every real product carries a relative
+error of about 2^-16, so the bound on max|diff| / max|ref| is 2e-4.  The split form
+(SPLIT_BF16X3) is then checked end to end against the FP64 oracle and the FP32 form.
+"""
+import numpy as np
+import pytest
+
+from oracle import model, mps
+
+pytestmark = pytest.mark.gpu
+TH_MID = model.initial_theta(model.TEMPERATURES["mid"])
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2511_23438_gb300 import build, lib
+    build.build()
+    lib.load()
+    return lib
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (64, 64, 64), (200, 130, 300), (1000, 70, 129),
+                                   (256, 512, 2048), (2048, 2048, 1024)])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_tc_gemm_matches_cuda_cores(L, M, N, K, mode):
+    err = L.tc_gemm_selftest(M, N, K, mode, seed=M * 7 + N * 13 + K + mode)
+    assert err < 2e-4, err
+
+
+def _evolve_random_state(L, prec, chi, steps, tmp_path, seed=5):
+    """Seeded random canonical MPS on the 5x6 grid, evolved by `steps` second-order steps on the
+    GPU (precision `prec`) and by the oracle; returns both (Z, Z2, X, F) after the last step."""
+    from test_gpu_parity import _random_canonical_blocks, _write_checkpoint
+    from oracle import layout
+    m = _random_canonical_blocks(5, 6, chi, seed=seed)
+    cfg = L.config(5, 6, chi, TH_MID, prec=prec)
+    p = str(tmp_path / ("rand_%s.bin" % prec))
+    _write_checkpoint(L, p, cfg, m, dtype=np.complex128 if prec == "fp64" else np.complex64)
+    g = L.MPS.load_checkpoint(p)
+    alpha, phi = model.layer_angles(-1.0, 2.0, 0.25, 2)
+    intra, inter = layout.schedule(5, 6)
+    for _ in range(steps):
+        m.x_layer(alpha)
+        m.zz_intra(phi, intra)
+        for gt in inter:
+            m.zz_inter(gt, phi)
+        m.x_layer(alpha)
+        g.step(-1.0, 2.0, 0.25, 2, 1)
+    z, z2, x, _ = m.observables()
+    o = g.observables()
+    return np.array([o["Z"], o["Z2"], o["X"], g.fidelity()]), np.array([z, z2, x, m.F]), min(m.cut_gaps)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16x3", "fp32"])
+def test_reduced_precision_forms_against_oracle(L, prec, tmp_path):
+    # 5x6 grid, d = 8, chi = 64 (block-sized contractions on the tensor cores in the split form),
+    # generic input (seeded random canonical MPS), two second-order steps
+    before = L.launch_count()
+    g, ref, gap = _evolve_random_state(L, prec, 64, 2, tmp_path)
+    assert L.launch_count() > before and gap > 1e-4
+    err = np.abs(g[:3] - ref[:3]).max()
+    ferr = abs(g[3] / ref[3] - 1)
+    print("%s vs FP64 oracle: max |d obs| %.2e, |dF/F| %.2e" % (prec, err, ferr))
+    assert err < 1e-3 and ferr < 1e-3
