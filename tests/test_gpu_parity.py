@@ -160,7 +160,7 @@ def test_odd_row_split_and_spectra(L):
         s = np.array(m.singular_values(bond))
         s_ref = np.asarray(s_ref)
         k = int(np.count_nonzero(s_ref > 1e-5 * s_ref[0]))
-        assert np.abs(s[:k] - s_ref[:k]).max() < TOL * s_ref[0]
+        assert np.abs(s[:k] - s_ref[:k]).max() < TOL_SMALL_S * s_ref[0]
 
 
 def test_closed_forms_on_gpu(L):
