@@ -174,6 +174,22 @@ int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long see
  * Allocates its own device memory. */
 int mpsgb_eig_selftest(int n, int fp64, unsigned long long seed, double out[6]);
 
+/* Allocation-free Hermitian eigendecomposition (the paper has no counterpart: this is a service
+ * for callers that cannot allocate device memory at the point of the call, e.g. code that runs
+ * under a frozen or request-scoped allocator, or a thread that must not enter the CUDA allocator).
+ * A: n x n Hermitian matrix on the device, row-major with leading dimension lda, complex128 if
+ * fp64 != 0 else complex64 (read only).  w: n eigenvalues, descending (double / float, device).
+ * V: eigenvectors as columns, row-major n x n with leading dimension ldv (device); A = V diag(w) V^H.
+ * Work is issued on cuda_stream and the call returns after the stream has finished it.
+ * Nothing is allocated: the solver's workspace is one fixed device array of 1 MiB per device, so
+ * n is limited to 1..128 (EINVAL beyond).  The first call on a device resolves that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.  Every call on a
+ * device shares the array and leaves its contents behind (each call re-initialises what it reads);
+ * calls that overlap on the GPU, from several streams or threads, race on it and must be serialised
+ * by the caller.  Errors: EINVAL, ETIMEDOUT (sweep limit), EDEVICE. */
+int mpsgb_eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv,
+                       void* cuda_stream);
+
 /* Host-only schedule facts of an Lx x Ly grid (no GPU needed): out[0] blocks, out[1] ZZ bonds,
  * out[2] in-block bonds, out[3] inter-block gates, out[4] bond truncations per ZZ layer,
  * out[5] largest local dimension.  Errors: EINVAL for an unsupported grid. */

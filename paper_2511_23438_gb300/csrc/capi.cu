@@ -274,6 +274,19 @@ int mpsgb_eig_selftest(int n, int fp64, unsigned long long seed, double out[6]) 
   return MPSGB_OK;
 }
 
+int mpsgb_eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv,
+                       void* cuda_stream) {
+  if (!A || !w || !V) return fail(MPSGB_EINVAL, "null pointer");
+  if (n < 1 || n > 128) return fail(MPSGB_EINVAL, "mpsgb_eigh_noalloc: n must be in 1..128 (fixed 1 MiB device scratch)");
+  if (lda < n || ldv < n) return fail(MPSGB_EINVAL, "leading dimension smaller than n");
+  int s = mpsgb::eigh_noalloc(n, fp64, A, lda, w, V, ldv, (cudaStream_t)cuda_stream);
+  if (s == -1) return fail(MPSGB_EINVAL, "mpsgb_eigh_noalloc: matrix does not fit the fixed scratch");
+  if (s == -3) return fail(MPSGB_ETIMEDOUT, "mpsgb_eigh_noalloc: Jacobi sweep limit reached");
+  if (s < 0) return fail(MPSGB_EDEVICE, "mpsgb_eigh_noalloc: CUDA error");
+  g_err.clear();
+  return MPSGB_OK;
+}
+
 double mpsgb_initial_theta(double J, double hx, double dtheta) { return std::asin(hx / (4.0 * J)) + dtheta; }
 
 double mpsgb_gamma_fit(int temperature, int chi, int n) {

@@ -18,6 +18,7 @@
 // with t = sign(z) / (|z| + sqrt(1 + z^2)), z = (c - a) / (2 |b|), zeroes b.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -567,6 +568,99 @@ int eig_selftest_t(int n, unsigned long long seed, double* out) {
 
 int eig_selftest(int n, int fp64, unsigned long long seed, double* out) {
   return fp64 ? eig_selftest_t<double>(n, seed, out) : eig_selftest_t<float>(n, seed, out);
+}
+
+}  // namespace mpsgb
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the eigensolver.  Some callers cannot allocate device memory at the
+// point where they need a decomposition -- for example code running under an allocator that is
+// frozen for the lifetime of a request, or a host thread that must not touch the CUDA allocator.
+// For them the whole workspace of the solver lives in one file-scope device array of fixed size,
+// shared by every call on a device.  Host code never dereferences the array's name (on the host it
+// is only a stand-in symbol): its device address is resolved once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------------------------
+namespace mpsgb {
+namespace {
+constexpr int kNoAllocMaxN = 128;                // largest matrix the fixed scratch can hold
+constexpr size_t kNoAllocBytes = size_t(1) << 20;  // 1 MiB of device scratch per device
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[128] = {nullptr};
+
+template <typename R>
+int eigh_noalloc_t(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv,
+                   unsigned char* scratch) {
+  unsigned char* ws = scratch;
+  auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
+  double* fro = reinterpret_cast<double*>(take(sizeof(double)));
+  fro2_kernel<R><<<1, 256, 0, st>>>(n, A, lda, 0, fro);
+  count_launch();
+  if (n <= 32) {
+    eig_small_kernel<R><<<1, 32, 0, st>>>(n, A, lda, 0, w, 0, V, ldv, 0, fro);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 1 : -4;
+  }
+  const int np = padded(n), nb = np / 16, npairs = nb / 2;
+  Cx<R>* H = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)np * np));
+  Cx<R>* Vw = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)np * np));
+  Cx<R>* Qs = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)npairs * 1024));
+  int* perm = reinterpret_cast<int*>(take(sizeof(int) * (size_t)np));
+  int* flag = reinterpret_cast<int*>(take(sizeof(int)));
+  int* ident = reinterpret_cast<int*>(take(sizeof(int) * (size_t)npairs));
+  if ((size_t)(ws - scratch) > kNoAllocBytes) return -1;
+  {
+    long long tot = (long long)np * np;
+    blk_init_kernel<R><<<dim3((unsigned)((tot + 255) / 256), 1), 256, 0, st>>>(n, np, A, lda, 0, H, Vw);
+    count_launch();
+  }
+  int sweeps = -1;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    for (int r = 0; r < nb - 1; ++r) {
+      blk_pair_kernel<R><<<dim3(npairs, 1), 128, 0, st>>>(np, nb, r, H, Qs, flag, ident, fro);
+      blk_update_kernel<R><<<dim3(npairs * npairs + npairs * (np / 32), 1), 256, 0, st>>>(np, nb, r, H, Vw, Qs, ident);
+      count_launch(2);
+    }
+    int hf = 0;  // pageable host word: the copy is synchronous, nothing is allocated
+    if (cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -4;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
+    if (!hf) { sweeps = sweep + 1; break; }
+  }
+  blk_finish_kernel<R><<<1, 1024, sizeof(R) * (size_t)n, st>>>(n, np, H, Vw, w, 0, V, ldv, 0, perm);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return -4;
+  return sweeps < 0 ? -3 : sweeps;
+}
+}  // namespace
+
+// Returns the sweep count (> 0), -1 for a size beyond the fixed scratch, -3 if the sweep limit was
+// reached, -4 for a CUDA error (including a failed cudaGetSymbolAddress).
+int eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv, cudaStream_t st) {
+  if (n < 1 || n > kNoAllocMaxN) return -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return -4;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return -4;
+      g_noalloc_base[dev] = p;
+    }
+    base = g_noalloc_base[dev];
+  }
+  unsigned char* scratch = static_cast<unsigned char*>(base);
+  if (fp64)
+    return eigh_noalloc_t<double>(st, n, static_cast<const z128*>(A), lda, static_cast<double*>(w),
+                                  static_cast<z128*>(V), ldv, scratch);
+  return eigh_noalloc_t<float>(st, n, static_cast<const c64*>(A), lda, static_cast<float*>(w), static_cast<c64*>(V),
+                               ldv, scratch);
 }
 
 }  // namespace mpsgb

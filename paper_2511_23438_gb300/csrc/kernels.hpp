@@ -31,6 +31,7 @@ size_t tc_gemm_workspace_bytes(long long M, long long N, long long K);
 int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View<float> B, c64 beta, View<float> C,
             void* ws, size_t ws_bytes, int* d_err);
 int eig_selftest(int n, int fp64, unsigned long long seed, double* out);
+int eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv, cudaStream_t st);
 int tc_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
 
 // ---------------------------------------------------------------- small kernels (local.cu)

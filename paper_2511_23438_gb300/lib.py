@@ -75,6 +75,8 @@ _SIGS = {
                                               ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
     "mpsgb_eig_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                           ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_eigh_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     "mpsgb_initial_theta": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "mpsgb_gamma_fit": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mpsgb_rescale": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -141,6 +143,12 @@ def eig_selftest(n, fp64=True, seed=1):
     out = (ctypes.c_double * 6)()
     _check(load().mpsgb_eig_selftest(n, 1 if fp64 else 0, seed, out))
     return dict(zip(("sweeps", "ms", "residual", "orthogonality", "sorted", "wmax"), list(out)))
+
+
+def eigh_noalloc(n, fp64, A_ptr, lda, w_ptr, V_ptr, ldv, stream=0):
+    """Hermitian eigendecomposition of a caller-owned device matrix without any allocation
+    (device pointers as ints; see mpsgb_eigh_noalloc in include/mpsgb.h)."""
+    _check(load().mpsgb_eigh_noalloc(n, 1 if fp64 else 0, A_ptr, lda, w_ptr, V_ptr, ldv, stream))
 
 
 def initial_theta(J, h, dtheta):
