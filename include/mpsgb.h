@@ -168,11 +168,13 @@ const char* mpsgb_kernel_site_name(int site);
 int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
 
 /* Self-test of the Hermitian eigensolver (no paper counterpart; a kernel check): a seeded n x n
- * positive semi-definite complex matrix with graded columns is decomposed in FP64 (fp64 != 0) or
- * FP32.  out[0] outer sweeps (-1: sweep limit), out[1] device ms, out[2] max |A V - V diag(w)| /
- * max |w|, out[3] max |V^H V - I| over sampled columns, out[4] 1 if w is descending, out[5] max |w|.
- * Allocates its own device memory. */
-int mpsgb_eig_selftest(int n, int fp64, unsigned long long seed, double out[6]);
+ * Hermitian complex matrix is decomposed in FP64 (fp64 != 0) or FP32.  kind 0: X X^H with graded
+ * columns of X (spectrum over many decades); kind 1: X X^H of rank n/2 (n - n/2 exact zeros);
+ * kind 2: [[I, P Q^H], [Q P^H, I]] with n/8 columns in P and Q (eigenvalue 1 with multiplicity
+ * n - 2(n/8) inside the spectrum).  out[0] outer sweeps, or the eigensolver's negative status,
+ * out[1] device ms, out[2] max |A V - V diag(w)| / max |w|, out[3] max |V^H V - I| over sampled
+ * columns, out[4] 1 if w is descending, out[5] max |w|.  Allocates its own device memory. */
+int mpsgb_eig_selftest(int n, int fp64, int kind, unsigned long long seed, double out[6]);
 
 /* Allocation-free Hermitian eigendecomposition (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory at the point of the call, e.g. code that runs

@@ -267,9 +267,9 @@ int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long see
   return MPSGB_OK;
 }
 
-int mpsgb_eig_selftest(int n, int fp64, unsigned long long seed, double out[6]) {
-  if (!out || n < 1 || n > 4096) return fail(MPSGB_EINVAL, "bad self-test arguments");
-  int s = mpsgb::eig_selftest(n, fp64, seed, out);
+int mpsgb_eig_selftest(int n, int fp64, int kind, unsigned long long seed, double out[6]) {
+  if (!out || n < 1 || n > 4096 || kind < 0 || kind > 2) return fail(MPSGB_EINVAL, "bad self-test arguments");
+  int s = mpsgb::eig_selftest(n, fp64, kind, seed, out);
   if (s != 0) return fail(MPSGB_EDEVICE, "CUDA error in the eigensolver self-test");
   return MPSGB_OK;
 }

@@ -395,6 +395,7 @@ inline int padded(int n) { return ((n + 31) / 32) * 32; }
 }  // namespace
 
 size_t eigh_workspace_bytes(int n, int batch, int real_bytes) {
+  if (n >= kTridiagMinN) return tri_workspace_bytes(n, real_bytes) + 4096;
   size_t c = 2 * (size_t)real_bytes;
   int np = padded(n);
   size_t b = 0;
@@ -415,6 +416,13 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
   double* fro = reinterpret_cast<double*>(take(sizeof(double) * batch));
   fro2_kernel<R><<<batch, 256, 0, st>>>(n, A, lda, sA, fro);
   count_launch();
+  if (n >= kTridiagMinN) {  // Householder tridiagonal route, one problem at a time
+    for (int b = 0; b < batch; ++b) {
+      int r = eigh_tridiag<R>(st, n, A + b * sA, lda, w + b * sw, V + b * sV, ldv, ws);
+      if (r < 0) return r;
+    }
+    return 1;
+  }
   if (n <= 32) {
     kt_begin(KT_EIG_SMALL, st);
     eig_small_kernel<R><<<batch, 32, 0, st>>>(n, A, lda, sA, w, sw, V, ldv, sV, fro);
@@ -482,7 +490,7 @@ namespace mpsgb {
 namespace {
 // A = X X^H / n + diag(shift) with seeded X (n x n): Hermitian positive semi-definite test matrix
 template <typename R>
-__global__ void psd_test_kernel(int n, Cx<R>* X, unsigned long long seed) {
+__global__ void psd_test_kernel(int n, Cx<R>* X, unsigned long long seed, int kind) {
   long long tot = (long long)n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
     unsigned long long h = (unsigned long long)i * 0x9E3779B97F4A7C15ULL + seed;
@@ -490,14 +498,15 @@ __global__ void psd_test_kernel(int n, Cx<R>* X, unsigned long long seed) {
     double a = (double)(h & 0xFFFFFF) / 16777216.0 - 0.5, b = (double)((h >> 24) & 0xFFFFFF) / 16777216.0 - 0.5;
     // graded columns: column j scaled by 2^{-j/4} so the spectrum spans many decades
     int j = (int)(i % n);
-    double sc = exp2(-0.25 * (j % 64));
+    double sc = kind == 2 ? 1.0 : exp2(-0.25 * (j % 64));
+    if (kind == 1 && j >= n / 2) sc = 0;  // rank n/2: n - n/2 exact zero eigenvalues
     X[i] = cmake<R>((R)(a * sc), (R)(b * sc));
   }
 }
 }  // namespace
 
 template <typename R>
-int eig_selftest_t(int n, unsigned long long seed, double* out) {
+int eig_selftest_t(int n, int kind, unsigned long long seed, double* out) {
   cudaStream_t st;
   if (cudaStreamCreate(&st) != cudaSuccess) return -4;
   Cx<R> *X, *A, *V;
@@ -509,9 +518,21 @@ int eig_selftest_t(int n, unsigned long long seed, double* out) {
   cudaMalloc(&V, sizeof(Cx<R>) * (size_t)n * n);
   cudaMalloc(&w, sizeof(R) * n);
   cudaMalloc(&ws, wsb);
-  psd_test_kernel<R><<<256, 256, 0, st>>>(n, X, seed);
+  psd_test_kernel<R><<<256, 256, 0, st>>>(n, X, seed, kind);
   Cx<R> one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
-  gemm<R>(st, n, n, n, one, rowmajor<R>(X, n), transposed<R>(X, n, true), zero, rowmajor<R>(A, n));
+  if (kind == 2) {
+    // A = [[I, P Q^H], [Q P^H, I]] with P, Q of n/8 columns: eigenvalues 1 +- sigma_k and a
+    // degenerate eigenvalue 1 of multiplicity n - 2 (n/8) in the middle of the spectrum
+    const int h = n / 2, k = std::max(1, n / 8);
+    Cx<R>* P = X;
+    Cx<R>* Q = X + (size_t)h * n;
+    set_identity<R>(st, n, A, n);
+    gemm<R>(st, h, n - h, k, one, rowmajor<R>(P, n), transposed<R>(Q, n, true), zero, rowmajor<R>(A + h, n));
+    gemm<R>(st, n - h, h, k, one, rowmajor<R>(Q, n), transposed<R>(P, n, true), zero,
+            rowmajor<R>(A + (size_t)h * n, n));
+  } else {
+    gemm<R>(st, n, n, n, one, rowmajor<R>(X, n), transposed<R>(X, n, true), zero, rowmajor<R>(A, n));
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -566,8 +587,8 @@ int eig_selftest_t(int n, unsigned long long seed, double* out) {
   return 0;
 }
 
-int eig_selftest(int n, int fp64, unsigned long long seed, double* out) {
-  return fp64 ? eig_selftest_t<double>(n, seed, out) : eig_selftest_t<float>(n, seed, out);
+int eig_selftest(int n, int fp64, int kind, unsigned long long seed, double* out) {
+  return fp64 ? eig_selftest_t<double>(n, kind, seed, out) : eig_selftest_t<float>(n, kind, seed, out);
 }
 
 }  // namespace mpsgb

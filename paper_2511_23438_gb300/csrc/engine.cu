@@ -237,7 +237,10 @@ class EngineT : public Engine {
   void eig(int n, C* A, R* w, C* V, void* ws, std::vector<double>& hw) {
     int sw = eigh<R>(stream, n, A, n, 0, w, 0, V, n, 0, 1, ws);
     stats.eig_calls++;
-    if (sw < 0) throw Fail{MPSGB_ETIMEDOUT, "Jacobi eigensolver did not converge within its sweep limit"};
+    if (sw == -1) throw Fail{MPSGB_ETIMEDOUT, "Jacobi eigensolver did not converge within its sweep limit"};
+    if (sw == -2) throw Fail{MPSGB_ETIMEDOUT, "eigensolver: a bounded grid barrier of the reduction timed out"};
+    if (sw == -3) throw Fail{MPSGB_ESTATE, "eigensolver: dependent eigenvectors could not be orthonormalised"};
+    if (sw < 0) throw Fail{MPSGB_EDEVICE, "eigensolver: launch or device error"};
     stats.eig_sweeps += sw;
     hbuf.resize(n);
     cudaMemcpyAsync(hbuf.data(), w, sizeof(R) * n, cudaMemcpyDeviceToHost, stream);

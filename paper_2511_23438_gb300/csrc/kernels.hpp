@@ -9,15 +9,28 @@ template <typename R>
 void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B, Cx<R> beta, View<R> C,
           int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
 
+// C = alpha op(A) op(B) + beta C on row-major real matrices (op(X) = X^T if tX); ws (ws_elems
+// elements, may be null) lets long-K products split K over CTAs with a fixed-order reduction.
+template <typename R>
+void rgemm(cudaStream_t st, int M, int N, int K, R alpha, const R* A, long long lda, bool ta, const R* B, long long ldb,
+           bool tb, R beta, R* C, long long ldc, R* ws, size_t ws_elems);
+
 // ---------------------------------------------------------------- eigensolver (eig.cu)
 // Hermitian eigendecomposition of `batch` n x n matrices (row-major, leading dim
 // lda, batch stride sA, read only).  Eigenvalues go to w (descending, stride sw),
 // eigenvectors to the columns of V (row-major n x n, leading dim ldv, stride sV):
 // A = V diag(w) V^H.  Cyclic parallel Jacobi: a warp-level solver for n <= 32 and a
 // blocked solver (16-wide blocks, 32 x 32 pair problems solved by warps, tile
-// updates of the full matrix) above.  Returns the number of outer sweeps, or -1 if
-// the sweep limit was hit without convergence.
+// updates of the full matrix) up to 64, Householder tridiagonalisation (tridiag.cu) above.
+// Returns the number of outer sweeps (1 for the tridiagonal route), or < 0: -1 Jacobi sweep
+// limit hit, -2 a bounded grid barrier of the reduction timed out, -3 the eigenvectors of the
+// tridiagonal matrix could not be orthonormalised (dependent vectors), -4 launch or device error.
 size_t eigh_workspace_bytes(int n, int batch, int real_bytes);
+// n above which eigh() uses the Householder-tridiagonal solver (tridiag.cu) instead of Jacobi
+constexpr int kTridiagMinN = 65;
+size_t tri_workspace_bytes(int n, int real_bytes);
+template <typename R>
+int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv, void* workspace);
 template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
          long long ldv, long long sV, int batch, void* workspace);
@@ -30,7 +43,7 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
 size_t tc_gemm_workspace_bytes(long long M, long long N, long long K);
 int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View<float> B, c64 beta, View<float> C,
             void* ws, size_t ws_bytes, int* d_err);
-int eig_selftest(int n, int fp64, unsigned long long seed, double* out);
+int eig_selftest(int n, int fp64, int kind, unsigned long long seed, double* out);
 int eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv, cudaStream_t st);
 int tc_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
 

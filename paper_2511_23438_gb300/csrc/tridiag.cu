@@ -1,0 +1,633 @@
+// Hermitian eigensolver for larger matrices: Householder reduction to a real symmetric
+// tridiagonal T, eigenvalues of T by bisection, eigenvectors of T by inverse iteration
+// (with modified Gram-Schmidt inside clusters of close eigenvalues), and back-transformation
+// of the eigenvectors with the Householder reflectors.
+//
+// 1. hetrd_kernel (cooperative, one CTA per SM): for column i the reflector
+//    H_i = I - tau_i v_i v_i^H (v_i[i+1] = 1) maps W[i+1:, i] to (beta, 0, ...), beta real;
+//    p = tau W22 v, w = p - (tau/2)(p^H v) v, W22 -= v w^H + w v^H.  Rows are owned
+//    cyclically by the CTAs; three bounded grid barriers per column (norm ready, p ready,
+//    update done).  T = Q^H A Q with Q = H_0 H_1 ... H_{n-2}; d = diag, e = sub-diagonal.
+// 2. bisect_kernel: eigenvalue j (descending) by bisection on the Sturm count of T.
+// 3. inverse_iter_kernel: one thread per eigenvector; LU with partial pivoting of
+//    (T - lambda_j I), three solves from a seeded start vector, normalised.
+// 4. cluster_mgs_kernel: one CTA per cluster of eigenvalues closer than ortol; modified
+//    Gram-Schmidt of its vectors in order.
+// 5. backtransform_kernel: one thread per column of Z applies H_{n-2} .. H_0 (X = Q Z).
+// Every grid barrier spins a bounded number of times; on timeout it records an error word.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace mpsgb {
+
+namespace {
+// Grid-wide barrier on a monotonic arrival counter: CTA thread 0 adds 1 with release semantics
+// and polls with acquire loads until `target` (= barrier index x gridDim.x) is reached.  The
+// wait is bounded by clock64(); on timeout it records err and continues, so the kernel always
+// finishes and the host reports the error.
+constexpr long long BAR_CYCLES = 4000000000LL;
+
+__device__ __forceinline__ void grid_sync(unsigned* count, unsigned target, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+    const long long t0 = clock64();
+    unsigned v;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (clock64() - t0 > BAR_CYCLES) { atomicExch(err, 1); break; }
+    }
+  }
+  __syncthreads();
+}
+
+// Householder reduction of the Hermitian n x n matrix A to real symmetric tridiagonal form.
+// Rows of the working copy W are owned cyclically by the CTAs.  Per column i:
+//   A. every CTA forms the reflector (beta, tau, v) of column i itself, v kept in shared memory;
+//      owned rows: p_r = tau (W22 v)_r (one warp per row) and a partial p^H v;      barrier 1
+//   B. every CTA loads p into shared memory; owned rows: W22 -= v w^H + w v^H with
+//      w = p - (tau/2)(p^H v) v; the Householder vector is stored in column i; the squared
+//      norm of the next column below its sub-diagonal is accumulated.               barrier 2
+// acc[0..1]: squared norm of column i (parity i & 1); acc[2..5]: p^H v (re, im) by parity.
+template <typename R>
+__global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long long lda, Cx<R>* W, R* d, R* e,
+                                                    Cx<R>* tau, Cx<R>* pb, double* acc, unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char hetrd_smem[];
+  Cx<R>* vs = reinterpret_cast<Cx<R>*>(hetrd_smem);
+  Cx<R>* ps = vs + n;
+  const int G = gridDim.x, c = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+  const int warp = t >> 5, lane = t & 31, nw = nt >> 5;
+  unsigned nbar = 0;
+  double nrm = 0;
+  for (int r = c; r < n; r += G) {
+    for (int j = t; j < n; j += nt) W[(long long)r * n + j] = A[(long long)r * lda + j];
+    if (r >= 2 && t == 0) nrm += (double)abs2(A[(long long)r * lda]);
+  }
+  if (t == 0 && nrm != 0) atomicAdd(&acc[0], nrm);
+  grid_sync(bar, (++nbar) * G, err);
+  for (int i = 0; i < n - 1; ++i) {
+    const int par = i & 1;
+    // ---- A: reflector of column i (same scalars in every CTA), v into shared memory
+    const Cx<R> alpha = W[(long long)(i + 1) * n + i];
+    const double xn2 = acc[par];
+    const double ar = alpha.x, ai = alpha.y;
+    double beta, tr, ti;
+    Cx<R> scale;
+    if (xn2 == 0.0 && ai == 0.0) {
+      beta = ar; tr = 0; ti = 0;
+      scale = cmake<R>(0, 0);
+    } else {
+      const double nrm_all = sqrt(ar * ar + ai * ai + xn2);
+      beta = ar >= 0 ? -nrm_all : nrm_all;
+      tr = (beta - ar) / beta;
+      ti = -ai / beta;
+      const double dr = ar - beta, di = ai, den = dr * dr + di * di;  // scale = 1 / (alpha - beta)
+      scale = cmake<R>((R)(dr / den), (R)(-di / den));
+    }
+    const Cx<R> tv = cmake<R>((R)tr, (R)ti);
+    for (int j = i + 1 + t; j < n; j += nt) vs[j] = j == i + 1 ? cmake<R>(1, 0) : scale * W[(long long)j * n + i];
+    if (c == 0 && t == 0) {
+      d[i] = W[(long long)i * n + i].x;
+      e[i] = (R)beta;
+      tau[i] = tv;
+    }
+    __syncthreads();
+    const int r0 = i + 1 + ((c - (i + 1)) % G + G) % G;
+    {
+      double dre = 0, dim = 0;
+      for (int r = r0 + warp * G; r < n; r += nw * G) {
+        Cx<R> sacc = cmake<R>(0, 0);
+        const Cx<R>* row = W + (long long)r * n;
+#pragma unroll 4
+        for (int j = i + 1 + lane; j < n; j += 32) cfma(sacc, row[j], vs[j]);
+        double sr = sacc.x, si = sacc.y;
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) {
+          const Cx<R> pv = tv * cmake<R>((R)sr, (R)si);
+          pb[r] = pv;
+          const Cx<R> v = vs[r];
+          dre += (double)pv.x * v.x + (double)pv.y * v.y;  // conj(p) v
+          dim += (double)pv.x * v.y - (double)pv.y * v.x;
+        }
+      }
+      if (lane == 0 && (dre != 0 || dim != 0)) {
+        atomicAdd(&acc[2 + 2 * par], dre);
+        atomicAdd(&acc[3 + 2 * par], dim);
+      }
+    }
+    grid_sync(bar, (++nbar) * G, err);
+    // ---- B: rank-2 update of the owned rows
+    for (int j = i + 1 + t; j < n; j += nt) ps[j] = pb[j];
+    const double pr = acc[2 + 2 * par], pi = acc[3 + 2 * par];
+    if (c == 0 && t == 0) {  // buffers of the other parity are free again
+      acc[par] = 0;
+      acc[2 + 2 * (par ^ 1)] = 0;
+      acc[3 + 2 * (par ^ 1)] = 0;
+    }
+    __syncthreads();
+    const Cx<R> a2 = cmake<R>((R)(-0.5 * (tr * pr - ti * pi)), (R)(-0.5 * (tr * pi + ti * pr)));
+    double nn = 0;
+    for (int r = r0; r < n; r += G) {
+      Cx<R>* row = W + (long long)r * n;
+      const Cx<R> vr = vs[r];
+      const Cx<R> wr = ps[r] + a2 * vr;
+      if (t == 0 && r > i + 1) row[i] = vr;  // Householder vector kept for the back-transformation
+#pragma unroll 4
+      for (int j = i + 1 + t; j < n; j += nt) {
+        const Cx<R> vj = vs[j];
+        const Cx<R> wj = ps[j] + a2 * vj;
+        Cx<R> x = row[j];
+        x = x - vr * conj(wj) - wr * conj(vj);
+        row[j] = x;
+        if (j == i + 1 && r >= i + 3) nn += (double)abs2(x);
+      }
+    }
+    if (nn != 0) atomicAdd(&acc[par ^ 1], nn);
+    grid_sync(bar, (++nbar) * G, err);
+  }
+  if (c == 0 && t == 0) d[n - 1] = W[(long long)(n - 1) * n + (n - 1)].x;
+}
+
+// number of eigenvalues of T smaller than x (Sturm sequence with a pivot floor)
+template <typename R>
+__device__ int sturm_count(int n, const R* d, const R* e, R x, R pivmin) {
+  int cnt = 0;
+  R q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0;
+  for (int k = 1; k < n; ++k) {
+    q = d[k] - x - e[k - 1] * e[k - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0;
+  }
+  return cnt;
+}
+
+// Eigenvalue k (ascending) of the unreduced block [blo[f], bhi[f]) that contains row f, with
+// k = f - blo[f], by multisection on the block's Sturm count: one warp per row f, the 32 lanes
+// evaluate 32 interior points, so every step shrinks the bracket 33-fold.
+template <typename R>
+__global__ void bisect_kernel(int n, const R* d, const R* e, const int* blo, const int* bhi, R* wf, R lo0, R hi0,
+                              R pivmin) {
+  const int f = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (f >= n) return;
+  const int s = blo[f], m = bhi[f] - s, idx = f - s;
+  R lo = lo0, hi = hi0;
+  const R eps = sizeof(R) == 8 ? R(2.2e-16) : R(1.2e-7);
+  for (int it = 0; it < 40; ++it) {
+    if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const R x = lo + (hi - lo) * (R)(lane + 1) / R(33);
+    const bool above = sturm_count<R>(m, d + s, e + s, x, pivmin) > idx;  // eigenvalue idx lies below x
+    const unsigned ball = __ballot_sync(0xffffffffu, above);
+    const int first = ball ? __ffs(ball) - 1 : 32;
+    const R nlo = first == 0 ? lo : lo + (hi - lo) * (R)first / R(33);
+    const R nhi = first == 32 ? hi : lo + (hi - lo) * (R)(first + 1) / R(33);
+    if (!(nlo > lo || nhi < hi)) break;  // no representable progress
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) wf[f] = R(0.5) * (lo + hi);
+}
+
+// Inverse iteration for output column j: eigenvalue wf[f] of block [blo[f], bhi[f]), f = perm[j].
+// (T_b - lambda I) z = b is solved by Gaussian elimination with partial pivoting on the block's
+// rows only, so the vector is supported on its block and vectors of different blocks are
+// exactly orthogonal.  The factors live in per-column scratch laid out [row][column] so that the
+// threads of a warp access consecutive words.
+template <typename R>
+__global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* perm, const R* wf, const int* blo,
+                                    const int* bhi, R* Z, R* U0, R* U1, R* U2, R* Lm, unsigned char* piv, R pfloor) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int f = perm[j];
+  const R lam = wf[f];
+  const int s = blo[f], t = bhi[f];
+  const long long K = n;
+  for (int i = 0; i < s; ++i) Z[i * K + j] = R(0);
+  for (int i = t; i < n; ++i) Z[i * K + j] = R(0);
+  // factor: rows of (T_b - lam I); U has diagonal U0 and two super-diagonals U1, U2
+  R a = d[s] - lam, b = t - s > 1 ? e[s] : R(0), cc = 0;  // current row: a (diag), b (super), cc (2nd super)
+  for (int i = s; i < t - 1; ++i) {
+    R below_sub = e[i], below_diag = d[i + 1] - lam, below_sup = (i + 2 < t) ? e[i + 1] : R(0);
+    if (fabs(a) >= fabs(below_sub)) {  // no row swap
+      R l = a == R(0) ? R(0) : below_sub / a;
+      if (fabs(a) < pfloor) a = a < R(0) ? -pfloor : pfloor;  // perturbed pivot (|l| <= 1 either way)
+      U0[i * K + j] = a; U1[i * K + j] = b; U2[i * K + j] = cc; Lm[i * K + j] = l; piv[i * K + j] = 0;
+      a = below_diag - l * b;
+      b = below_sup - l * cc;
+      cc = 0;
+    } else {  // swap rows i and i+1
+      R l = a / below_sub;
+      U0[i * K + j] = below_sub; U1[i * K + j] = below_diag; U2[i * K + j] = below_sup; Lm[i * K + j] = l;
+      piv[i * K + j] = 1;
+      R na = b - l * below_diag;
+      R nb = cc - l * below_sup;
+      a = na; b = nb; cc = 0;
+    }
+  }
+  if (fabs(a) < pfloor) a = a < R(0) ? -pfloor : pfloor;
+  U0[(long long)(t - 1) * K + j] = a;
+  U1[(long long)(t - 1) * K + j] = 0;
+  U2[(long long)(t - 1) * K + j] = 0;
+  // seeded start vector (distinct per j so that equal shifts give independent vectors)
+  for (int i = s; i < t; ++i) {
+    unsigned long long h = (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL + (unsigned long long)(j + 7) * 0xD1B54A32D192ED03ULL;
+    h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ULL; h ^= h >> 29;
+    Z[i * K + j] = (R)((double)(h & 0xFFFFFF) / 16777216.0 + 0.5);
+  }
+  for (int iter = 0; iter < 3; ++iter) {
+    // forward: apply L (with the recorded swaps) to z
+    for (int i = s; i < t - 1; ++i) {
+      R zi = Z[i * K + j], zn = Z[(i + 1) * K + j];
+      if (piv[i * K + j]) { R tmp = zi; zi = zn; zn = tmp; }
+      Z[i * K + j] = zi;
+      Z[(i + 1) * K + j] = zn - Lm[i * K + j] * zi;
+    }
+    // backward: U z = y
+    R z2 = 0, z1 = 0;
+    for (int i = t - 1; i >= s; --i) {
+      R v = (Z[i * K + j] - U1[i * K + j] * z1 - U2[i * K + j] * z2) / U0[i * K + j];
+      Z[i * K + j] = v;
+      z2 = z1; z1 = v;
+    }
+    // normalise (scaled by the largest entry first, so that squares cannot overflow)
+    double mx = 0, sq = 0;
+    for (int i = s; i < t; ++i) mx = fmax(mx, fabs((double)Z[i * K + j]));
+    if (!(mx > 0) || !(mx < 1e300)) mx = 1;
+    for (int i = s; i < t; ++i) { const double z = Z[i * K + j] / mx; sq += z * z; }
+    const double inv = 1.0 / (mx * sqrt(sq));
+    for (int i = s; i < t; ++i) Z[i * K + j] = (R)(Z[i * K + j] * inv);
+  }
+}
+
+// Modified Gram-Schmidt, in order, of the columns cidx[coff[c] .. coff[c+1]) of Z (one cluster of
+// close eigenvalues of one unreduced block per CTA); the vectors live on rows [rlo[c], rhi[c]).
+template <typename R>
+__global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, const int* cidx, const int* coff,
+                                                          const int* rlo, const int* rhi) {
+  __shared__ double red[32];
+  const int c0 = coff[blockIdx.x], c1 = coff[blockIdx.x + 1];
+  const int r0 = rlo[blockIdx.x], r1 = rhi[blockIdx.x];
+  const long long K = n;
+  auto block_dot = [&](int x, int y) {
+    double s = 0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += (double)Z[r * K + x] * Z[r * K + y];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double tot = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += red[q];
+    return tot;
+  };
+  for (int a = c0; a < c1; ++a) {
+    const int jv = cidx[a];
+    for (int b = c0; b < a; ++b) {
+      const int ip = cidx[b];
+      const double tot = block_dot(ip, jv);
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Z[r * K + jv] -= (R)tot * Z[r * K + ip];
+      __syncthreads();
+    }
+    const R inv = (R)(1.0 / sqrt(block_dot(jv, jv)));
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Z[r * K + jv] *= inv;
+    __syncthreads();
+  }
+}
+
+// Panel of nb Householder vectors (columns i0 .. i0+nb-1 of W) as an explicit (n - i0 - 1) x nb
+// matrix: v_j has a unit entry at row i0 + j + 1, W[r][i0 + j] below it and zeros above.
+template <typename R>
+__global__ void panel_kernel(int n, int i0, int nb, const Cx<R>* W, Cx<R>* P) {
+  const int m = n - i0 - 1;
+  const long long tot = (long long)m * nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int rr = (int)(e / nb), j = (int)(e - (long long)rr * nb);
+    int r = i0 + 1 + rr;  // global row
+    Cx<R> v = cmake<R>(0, 0);
+    if (r == i0 + j + 1) v = cmake<R>(1, 0);
+    else if (r > i0 + j + 1) v = W[(long long)r * n + i0 + j];
+    P[e] = v;
+  }
+}
+
+// Compact-WY factor T (nb x nb, upper triangular) of H_{i0} ... H_{i0+nb-1} = I - V T V^H from
+// S = V^H V: T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] S[0:j, j].
+template <typename R>
+__global__ void wy_t_kernel(int nb, const Cx<R>* S, const Cx<R>* tau, Cx<R>* T) {
+  if (threadIdx.x != 0) return;
+  for (int a = 0; a < nb * nb; ++a) T[a] = cmake<R>(0, 0);
+  for (int j = 0; j < nb; ++j) {
+    const Cx<R> tj = tau[j];
+    T[j * nb + j] = tj;
+    for (int a = 0; a < j; ++a) {
+      Cx<R> acc = cmake<R>(0, 0);
+      for (int b = a; b < j; ++b) cfma(acc, T[a * nb + b], S[b * nb + j]);
+      T[a * nb + j] = cmake<R>(R(0), R(0)) - tj * acc;
+    }
+  }
+}
+
+// Real G (nb x nb symmetric positive definite, nb <= 64) = R^T R with R upper triangular
+// (right-looking Cholesky, thread c owns column c); writes R^{-1} (nb x nb, row-major).  One shared
+// array: R's strict upper part above the diagonal, R^{-1} transposed on and below it, diag(R) apart.
+// A non-positive pivot sets err and is clamped.
+template <typename R>
+__global__ void __launch_bounds__(64) chol_inv_kernel(int nb, const R* G, R* Rinv, int* err) {
+  __shared__ R A[64 * 65];
+  __shared__ R dR[64];
+  const int c = threadIdx.x;
+  for (int r = 0; r < nb; ++r)
+    if (c < nb) A[r * 65 + c] = G[r * nb + c];
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    R piv = A[j * 65 + j];
+    if (!(piv > R(0))) {
+      if (c == 0) atomicExch(err, 2);
+      piv = sizeof(R) == 8 ? R(1e-300) : R(1e-30);
+    }
+    const R rjj = sqrt(piv);
+    __syncthreads();
+    if (c > j && c < nb) A[j * 65 + c] /= rjj;
+    if (c == j) dR[j] = rjj;
+    __syncthreads();
+    if (c > j && c < nb)
+      for (int r = j + 1; r <= c; ++r) A[r * 65 + c] -= A[j * 65 + r] * A[j * 65 + c];
+    __syncthreads();
+  }
+  if (c < nb) {  // column c of R^{-1} by back substitution, stored as row c of the lower part
+    for (int r = c; r >= 0; --r) {
+      R v = r == c ? R(1) : R(0);
+      for (int k = r + 1; k <= c; ++k) v -= A[r * 65 + k] * A[c * 65 + k];
+      A[c * 65 + r] = v / dR[r];
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < nb; ++r)
+    if (c < nb) Rinv[r * nb + c] = r <= c ? A[c * 65 + r] : R(0);
+}
+
+// dst[r * ldd + c] = src[r * lds + c] for an m x k real block
+template <typename R>
+__global__ void copy_real_kernel(int m, int k, const R* src, long long lds, R* dst, long long ldd) {
+  const long long tot = (long long)m * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+    dst[(e / k) * ldd + e % k] = src[(e / k) * lds + e % k];
+}
+
+template <typename R>
+__global__ void real_to_complex_kernel(long long cnt, const R* Z, Cx<R>* X) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cnt; e += (long long)gridDim.x * blockDim.x)
+    X[e] = cmake<R>(Z[e], R(0));
+}
+}  // namespace
+
+size_t tri_workspace_bytes(int n, int real_bytes) {
+  size_t c = 2 * (size_t)real_bytes, nn = (size_t)n * n;
+  size_t b = 0;
+  b += nn * c;                   // W
+  b += nn * c;                   // X (back-transform)
+  b += 5 * nn * real_bytes;      // Z, U0, U1, U2, L
+  b += nn;                       // pivots
+  b += 8 * (size_t)n * c;        // d, e, tau, v, p, w, cluster bounds
+  b += 6 * (size_t)n * 8 + 8 * 256;  // block eigenvalues, block bounds, permutation, cluster lists
+  b += 3 * 32 * (size_t)n * c + 2 * 32 * 32 * c + 7 * 256;  // WY panel, Y1, Y2, S, T
+  b += (size_t)(8 + 2) * n * 64 * (c / 2) + 2 * 64 * 64 * (c / 2) + 5 * 256;  // real orthonormalisation
+  return b + 64 * 1024;
+}
+
+// Returns 1, -3 if a grid barrier of the reduction timed out, -4 on a CUDA error.
+template <typename R>
+int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv, void* workspace) {
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
+  const size_t nn = (size_t)n * n;
+  Cx<R>* Wm = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * nn));
+  Cx<R>* X = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * nn));
+  R* Z = reinterpret_cast<R*>(take(sizeof(R) * nn));
+  R* U0 = reinterpret_cast<R*>(take(sizeof(R) * nn));
+  R* U1 = reinterpret_cast<R*>(take(sizeof(R) * nn));
+  R* U2 = reinterpret_cast<R*>(take(sizeof(R) * nn));
+  R* Lm = reinterpret_cast<R*>(take(sizeof(R) * nn));
+  unsigned char* piv = take(nn);
+  R* dv = reinterpret_cast<R*>(take(sizeof(R) * n));
+  R* ev = reinterpret_cast<R*>(take(sizeof(R) * n));
+  Cx<R>* tau = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * n));
+  Cx<R>* pb = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * n));
+  Cx<R>* Pn = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)n * 32));
+  Cx<R>* Sm = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * 32 * 32));
+  Cx<R>* Tm = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * 32 * 32));
+  Cx<R>* Y1 = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)n * 32));
+  Cx<R>* Y2 = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)n * 32));
+  const size_t wr_elems = (size_t)8 * n * 64;
+  R* Wr = reinterpret_cast<R*>(take(sizeof(R) * wr_elems));
+  R* Cr = reinterpret_cast<R*>(take(sizeof(R) * (size_t)n * 64));
+  R* Yr = reinterpret_cast<R*>(take(sizeof(R) * (size_t)n * 64));
+  R* Sr = reinterpret_cast<R*>(take(sizeof(R) * 64 * 64));
+  R* Tr = reinterpret_cast<R*>(take(sizeof(R) * 64 * 64));
+  R* wf = reinterpret_cast<R*>(take(sizeof(R) * n));
+  int* blo = reinterpret_cast<int*>(take(sizeof(int) * n));
+  int* bhi = reinterpret_cast<int*>(take(sizeof(int) * n));
+  int* perm = reinterpret_cast<int*>(take(sizeof(int) * n));
+  int* cl_idx = reinterpret_cast<int*>(take(sizeof(int) * n));
+  int* cl_off = reinterpret_cast<int*>(take(sizeof(int) * (n + 1)));
+  int* cl_rlo = reinterpret_cast<int*>(take(sizeof(int) * n));
+  int* cl_rhi = reinterpret_cast<int*>(take(sizeof(int) * n));
+  double* acc = reinterpret_cast<double*>(take(sizeof(double) * 8));
+  unsigned* bar = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * 4));
+  int* d_err = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
+  cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, st);
+  cudaMemsetAsync(d_err, 0, sizeof(int) * 4, st);
+  // optional phase timing (MPSGB_TRI_PROFILE=1): event pairs around each phase, printed to stderr
+  static const bool prof = std::getenv("MPSGB_TRI_PROFILE") != nullptr;
+  cudaEvent_t pev[6] = {nullptr};
+  if (prof) for (auto& x : pev) cudaEventCreate(&x);
+  if (prof) cudaEventRecord(pev[0], st);
+  // ---- 1. tridiagonalisation (cooperative persistent kernel, one CTA per SM)
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t hsm = 2 * sizeof(Cx<R>) * (size_t)n;  // v and p of the current column
+  if (hsm > 200 * 1024) return -4;
+  if (hsm > 48 * 1024 &&
+      cudaFuncSetAttribute(hetrd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm) != cudaSuccess)
+    return -4;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hetrd_kernel<R>, 512, hsm);
+  if (per_sm < 1) return -4;
+  int grid = sms;
+  int n_ = n;
+  long long lda_ = lda;
+  void* args[] = {&n_, (void*)&A, &lda_, &Wm, &dv, &ev, &tau, &pb, &acc, &bar, &d_err};
+  kt_begin(KT_OTHER, st);
+  if (cudaLaunchCooperativeKernel((void*)hetrd_kernel<R>, dim3(grid), dim3(512), args, hsm, st) != cudaSuccess) return -4;
+  kt_end(KT_OTHER, st);
+  count_launch();
+  if (prof) cudaEventRecord(pev[1], st);
+  // ---- 2. split T at negligible off-diagonal entries (|e_i| <= 32 eps ||T||, an absolute
+  // perturbation of the order of the reduction's own backward error); eigenvalues of each
+  // unreduced block by bisection (Gershgorin interval from the host copy of T)
+  std::vector<R> hd(n), he(n);
+  int herr = 0;
+  cudaMemcpyAsync(hd.data(), dv, sizeof(R) * n, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(he.data(), ev, sizeof(R) * n, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
+  if (herr != 0) return -2;
+  double lo = 1e300, hi = -1e300, emax2 = 0, tnorm = 0;
+  for (int i = 0; i < n; ++i) {
+    double off = (i > 0 ? std::fabs((double)he[i - 1]) : 0) + (i < n - 1 ? std::fabs((double)he[i]) : 0);
+    lo = std::min(lo, (double)hd[i] - off);
+    hi = std::max(hi, (double)hd[i] + off);
+    if (i < n - 1) emax2 = std::max(emax2, (double)he[i] * he[i]);
+    tnorm = std::max(tnorm, std::fabs((double)hd[i]) + off);
+  }
+  const double eps = sizeof(R) == 8 ? 2.2e-16 : 1.2e-7;
+  const double safmin = sizeof(R) == 8 ? 2.3e-308 : 1.2e-38;
+  const R pivmin = (R)(safmin * std::max(1.0, emax2) * 4);
+  lo -= 4 * eps * tnorm + 2 * pivmin;
+  hi += 4 * eps * tnorm + 2 * pivmin;
+  const double tol_split = 32 * eps * tnorm;
+  std::vector<int> hblo(n), hbhi(n);
+  for (int i = 0, s0 = 0; i < n; ++i) {
+    const bool last = i == n - 1 || std::fabs((double)he[i]) <= tol_split;
+    if (i < n - 1 && last) he[i] = R(0);
+    if (last) {
+      for (int r = s0; r <= i; ++r) { hblo[r] = s0; hbhi[r] = i + 1; }
+      s0 = i + 1;
+    }
+  }
+  cudaMemcpyAsync(ev, he.data(), sizeof(R) * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(blo, hblo.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(bhi, hbhi.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  bisect_kernel<R><<<(n + 3) / 4, 128, 0, st>>>(n, dv, ev, blo, bhi, wf, (R)lo, (R)hi, pivmin);
+  count_launch();
+  // all eigenvalues in descending order (ties in row order), w and the column permutation
+  std::vector<R> hwf(n);
+  cudaMemcpyAsync(hwf.data(), wf, sizeof(R) * n, cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
+  std::vector<int> hperm(n);
+  for (int i = 0; i < n; ++i) hperm[i] = i;
+  std::stable_sort(hperm.begin(), hperm.end(), [&](int x, int y) { return hwf[x] > hwf[y]; });
+  std::vector<R> hw(n);
+  for (int j = 0; j < n; ++j) hw[j] = hwf[hperm[j]];
+  cudaMemcpyAsync(perm, hperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(w, hw.data(), sizeof(R) * n, cudaMemcpyHostToDevice, st);
+  if (prof) cudaEventRecord(pev[2], st);
+  // ---- 3. eigenvectors of the blocks by inverse iteration
+  // pivots of (T_b - lambda I) are kept at least eps ||T|| in magnitude: a perturbation of the size
+  // of the eigenvalue error that also bounds the growth of the solution
+  const R pfloor = (R)std::max(eps * tnorm, (double)pivmin);
+  inverse_iter_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(n, dv, ev, perm, wf, blo, bhi, Z, U0, U1, U2, Lm, piv, pfloor);
+  count_launch();
+  if (prof) cudaEventRecord(pev[3], st);
+  // ---- 4. clusters of close eigenvalues: re-orthogonalise
+  // clusters: within one unreduced block, runs of eigenvalues closer than ortol (vectors of
+  // different blocks are orthogonal by construction), re-orthogonalised in chunks of at most 64
+  const double ortol = (sizeof(R) == 8 ? 1e-10 : 1e-6) * std::max(tnorm, 1e-300);
+  std::vector<int> cidx, coff(1, 0), crlo, crhi;
+  {
+    std::vector<int> order(n);  // sorted positions grouped by block, descending within a block
+    for (int j = 0; j < n; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hblo[hperm[x]] < hblo[hperm[y]]; });
+    for (int q = 0; q < n;) {
+      const int blk = hblo[hperm[order[q]]];
+      int q1 = q + 1;
+      while (q1 < n && hblo[hperm[order[q1]]] == blk && (double)hw[order[q1 - 1]] - (double)hw[order[q1]] < ortol) ++q1;
+      for (int a0 = q; q1 - q > 1 && a0 < q1; a0 += 64) {
+        for (int a = a0; a < std::min(q1, a0 + 64); ++a) cidx.push_back(order[a]);
+        coff.push_back((int)cidx.size());
+        crlo.push_back(blk);
+        crhi.push_back(hbhi[hperm[order[q]]]);
+      }
+      q = q1;
+    }
+  }
+  const size_t ncl = crlo.size();
+  if (ncl > 0) {
+    cudaMemcpyAsync(cl_idx, cidx.data(), sizeof(int) * cidx.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(cl_off, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(cl_rlo, crlo.data(), sizeof(int) * ncl, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(cl_rhi, crhi.data(), sizeof(int) * ncl, cudaMemcpyHostToDevice, st);
+    cluster_mgs_kernel<R><<<(unsigned)ncl, 256, 0, st>>>(n, Z, cl_idx, cl_off, cl_rlo, cl_rhi);
+    count_launch();
+  }
+  if (prof) cudaEventRecord(pev[4], st);
+  // ---- 5. back-transformation
+  {
+    // X = Q Z with Q = H_0 ... H_{n-2}, applied block by block from the last one:
+    // X[i0+1:, :] <- (I - V T V^H) X[i0+1:, :]
+    const int NB = 32;
+    const long long nn_ = (long long)n * n;
+    // Orthonormalise the eigenvectors of T (real, columns of Z) in descending-eigenvalue order:
+    // each block of 64 columns is projected twice against all earlier columns (block classical
+    // Gram-Schmidt) and then made orthonormal by Cholesky-QR, also twice.  Inverse iteration
+    // leaves the vectors of well-separated eigenvalues orthogonal to working precision, so they
+    // are unchanged; the vectors of close eigenvalues are made orthogonal.
+    for (int b0 = 0; b0 < n; b0 += 64) {
+      const int nb = std::min(64, n - b0);
+      R* Zb = Z + b0;
+      for (int pass = 0; pass < 2 && b0 > 0; ++pass) {
+        rgemm<R>(st, b0, nb, n, R(1), Z, n, true, Zb, n, false, R(0), Cr, nb, Wr, wr_elems);
+        rgemm<R>(st, n, nb, b0, R(-1), Z, n, false, Cr, nb, false, R(1), Zb, n, Wr, wr_elems);
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        rgemm<R>(st, nb, nb, n, R(1), Zb, n, true, Zb, n, false, R(0), Sr, nb, Wr, wr_elems);
+        chol_inv_kernel<R><<<1, 64, 0, st>>>(nb, Sr, Tr, d_err + 1);
+        rgemm<R>(st, n, nb, nb, R(1), Zb, n, false, Tr, nb, false, R(0), Yr, nb, Wr, wr_elems);
+        copy_real_kernel<R><<<256, 256, 0, st>>>(n, nb, Yr, nb, Zb, n);
+        count_launch();
+        count_launch();
+      }
+    }
+    real_to_complex_kernel<R><<<1024, 256, 0, st>>>(nn_, Z, X);
+    count_launch();
+    const Cx<R> one = cmake<R>(1, 0), zero = cmake<R>(0, 0), mone = cmake<R>(-1, 0);
+    const int nref = n - 1;
+    for (int i0 = ((nref - 1) / NB) * NB; i0 >= 0; i0 -= NB) {
+      const int nb = std::min(NB, nref - i0);
+      const int m = n - i0 - 1;
+      panel_kernel<R><<<256, 256, 0, st>>>(n, i0, nb, Wm, Pn);
+      count_launch();
+      // S = V^H V, T from S, Y = V^H X, Y2 = T Y, X -= V Y2
+      gemm<R>(st, nb, nb, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Pn, nb), zero, rowmajor<R>(Sm, nb));
+      wy_t_kernel<R><<<1, 32, 0, st>>>(nb, Sm, tau + i0, Tm);
+      count_launch();
+      Cx<R>* Xs = X + (long long)(i0 + 1) * n;
+      gemm<R>(st, nb, n, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n));
+      gemm<R>(st, nb, n, nb, one, rowmajor<R>(Tm, nb), rowmajor<R>(Y1, n), zero, rowmajor<R>(Y2, n));
+      gemm<R>(st, m, n, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
+    }
+    copy_view<R, R>(st, n, n, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
+  }
+  if (prof) {
+    cudaEventRecord(pev[5], st);
+    cudaEventSynchronize(pev[5]);
+    float t[5];
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], pev[i], pev[i + 1]);
+    std::fprintf(stderr, "tridiag n=%d fp%d: hetrd %.2f bisect %.2f inviter %.2f mgs %.2f (clusters %zu) back %.2f ms\n", n,
+                 (int)(8 * sizeof(R)), t[0], t[1], t[2], t[3], ncl, t[4]);
+    for (auto& x : pev) cudaEventDestroy(x);
+  }
+  int cherr = 0;
+  cudaMemcpyAsync(&cherr, d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -4;
+  return cherr != 0 ? -3 : 1;
+}
+
+template int eigh_tridiag<double>(cudaStream_t, int, const z128*, long long, double*, z128*, long long, void*);
+template int eigh_tridiag<float>(cudaStream_t, int, const c64*, long long, float*, c64*, long long, void*);
+
+}  // namespace mpsgb

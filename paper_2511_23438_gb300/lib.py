@@ -73,7 +73,7 @@ _SIGS = {
     "mpsgb_kernel_site_name": (ctypes.c_char_p, [ctypes.c_int]),
     "mpsgb_tc_gemm_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
-    "mpsgb_eig_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+    "mpsgb_eig_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                           ctypes.POINTER(ctypes.c_double)]),
     "mpsgb_eigh_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
@@ -139,9 +139,9 @@ def tc_gemm_selftest(M, N, K, mode=0, seed=1):
     return e.value
 
 
-def eig_selftest(n, fp64=True, seed=1):
+def eig_selftest(n, fp64=True, seed=1, kind=0):
     out = (ctypes.c_double * 6)()
-    _check(load().mpsgb_eig_selftest(n, 1 if fp64 else 0, seed, out))
+    _check(load().mpsgb_eig_selftest(n, 1 if fp64 else 0, kind, seed, out))
     return dict(zip(("sweeps", "ms", "residual", "orthogonality", "sorted", "wmax"), list(out)))
 
 
