@@ -43,7 +43,7 @@ __device__ __forceinline__ void ld4(const Cx<R>* p, Cx<R>* out) {  // 4 consecut
 template <typename R, int TM>
 __global__ void __launch_bounds__(256, 1) cgemm_kernel(int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B,
                                                        Cx<R> beta, View<R> C, long long sA, long long sB,
-                                                       long long sC) {
+                                                       long long sC, int kchunk) {
   using Tl = CTile<R, TM>;
   constexpr int T = Tl::T, LD = Tl::LD, PER = Tl::PER, G = TM / 4;
   __shared__ __align__(16) Cx<R> As[2][CK][LD];
@@ -54,6 +54,9 @@ __global__ void __launch_bounds__(256, 1) cgemm_kernel(int M, int N, int K, Cx<R
   const Cx<R>* Ap = A.ptr + z * sA;
   const Cx<R>* Bp = B.ptr + z * sB;
   Cx<R>* Cp = C.ptr + z * sC;
+  // split K (kchunk > 0): slice z covers k in [z kchunk, (z+1) kchunk); A and B are shared
+  const int kbeg = kchunk > 0 ? (int)z * kchunk : 0;
+  const int kend = kchunk > 0 ? min(K, kbeg + kchunk) : K;
   // A: contiguous along k (row-major) -> k fastest in the thread mapping, else i fastest
   const bool a_kfast = A.col.inner == 0 && A.col.stride == 1;
   const bool b_kfast = B.row.inner == 0 && B.row.stride == 1;
@@ -73,11 +76,11 @@ __global__ void __launch_bounds__(256, 1) cgemm_kernel(int M, int N, int K, Cx<R
     for (int u = 0; u < PER; ++u) {
       const int k = k0 + ak[u];
       Cx<R> v = cmake<R>(0, 0);
-      if (aro[u] >= 0 && k < K) { v = Ap[aro[u] + A.col(k)]; if (A.conj) v.y = -v.y; }
+      if (aro[u] >= 0 && k < kend) { v = Ap[aro[u] + A.col(k)]; if (A.conj) v.y = -v.y; }
       pa[u] = v;
       const int kb = k0 + bk[u];
       Cx<R> w = cmake<R>(0, 0);
-      if (bco[u] >= 0 && kb < K) { w = Bp[B.row(kb) + bco[u]]; if (B.conj) w.y = -w.y; }
+      if (bco[u] >= 0 && kb < kend) { w = Bp[B.row(kb) + bco[u]]; if (B.conj) w.y = -w.y; }
       pb[u] = w;
     }
   };
@@ -93,12 +96,12 @@ __global__ void __launch_bounds__(256, 1) cgemm_kernel(int M, int N, int K, Cx<R
   for (int a = 0; a < TM; ++a)
 #pragma unroll
     for (int b = 0; b < TM; ++b) acc[a][b] = cmake<R>(0, 0);
-  fetch(0);
+  fetch(kbeg);
   stash(0);
   __syncthreads();
   int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += CK) {
-    const bool more = k0 + CK < K;
+  for (int k0 = kbeg; k0 < kend; k0 += CK) {
+    const bool more = k0 + CK < kend;
     if (more) fetch(k0 + CK);
 #pragma unroll
     for (int kk = 0; kk < CK; ++kk) {
@@ -136,7 +139,53 @@ __global__ void __launch_bounds__(256, 1) cgemm_kernel(int M, int N, int K, Cx<R
     }
   }
 }
+// C = alpha * sum_z W[z] + beta * C (the split-K partial products, summed in a fixed order)
+template <typename R>
+__global__ void csplit_reduce_kernel(int M, int N, int splits, Cx<R> alpha, const Cx<R>* W, Cx<R> beta, View<R> C) {
+  const long long tot = (long long)M * N;
+  const bool use_beta = (beta.x != R(0) || beta.y != R(0));
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    Cx<R> s = cmake<R>(0, 0);
+    for (int zz = 0; zz < splits; ++zz) s = s + W[zz * tot + e];
+    const int i = (int)(e / N), j = (int)(e % N);
+    const long long o = C.row(i) + C.col(j);
+    Cx<R> v = alpha * s;
+    if (use_beta) v = v + beta * C.ptr[o];
+    C.ptr[o] = v;
+  }
+}
 }  // namespace
+
+template <typename R>
+void gemm_splitk(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B, Cx<R> beta, View<R> C,
+                 Cx<R>* ws, size_t ws_elems) {
+  if (M <= 0 || N <= 0) return;
+  const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
+  int splits = (int)std::min<long long>((2 * 152 + tiles - 1) / tiles, K / 64);
+  while (splits > 1 && (size_t)splits * M * N > ws_elems) --splits;
+  if (splits <= 1 || ws == nullptr) {
+    gemm<R>(st, M, N, K, alpha, A, B, beta, C);
+    return;
+  }
+  const int kchunk = ((K + splits - 1) / splits + CK - 1) / CK * CK;
+  splits = (K + kchunk - 1) / kchunk;
+  View<R> W = rowmajor<R>(ws, N);
+  kt_begin(KT_GEMM, st);
+  dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
+  cgemm_kernel<R, 4><<<grid, 256, 0, st>>>(M, N, K, cmake<R>(1, 0), A, B, cmake<R>(0, 0), W, 0, 0, (long long)M * N,
+                                           kchunk);
+  const long long tot = (long long)M * N;
+  csplit_reduce_kernel<R><<<(unsigned)std::min<long long>((tot + 255) / 256, 1216), 256, 0, st>>>(M, N, splits, alpha,
+                                                                                                  ws, beta, C);
+  kt_end(KT_GEMM, st);
+  kt_add_work(KT_GEMM, 8.0 * M * N * (double)K);
+  count_launch(2);
+}
+
+template void gemm_splitk<double>(cudaStream_t, int, int, int, z128, View<double>, View<double>, z128, View<double>,
+                                  z128*, size_t);
+template void gemm_splitk<float>(cudaStream_t, int, int, int, c64, View<float>, View<float>, c64, View<float>, c64*,
+                                 size_t);
 
 template <typename R>
 void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B, Cx<R> beta, View<R> C, int batch,
@@ -154,12 +203,12 @@ void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> 
     if (t128 >= 148) {
       big = true;
       dim3 grid((N + 127) / 128, (M + 127) / 128, batch);
-      cgemm_kernel<R, 8><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C, sA, sB, sC);
+      cgemm_kernel<R, 8><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C, sA, sB, sC, 0);
     }
   }
   if (!big) {
     dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
-    cgemm_kernel<R, 4><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C, sA, sB, sC);
+    cgemm_kernel<R, 4><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C, sA, sB, sC, 0);
   }
   kt_end(KT_GEMM, st);
   kt_add_work(KT_GEMM, 8.0 * M * N * (double)K * batch);

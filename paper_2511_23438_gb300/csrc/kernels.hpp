@@ -9,6 +9,11 @@ template <typename R>
 void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B, Cx<R> beta, View<R> C,
           int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
 
+// As gemm (batch 1), with K split over CTAs into the workspace ws (ws_elems complex elements) and
+// reduced in a fixed order when the output alone has too few tiles to fill the GPU.
+template <typename R>
+void gemm_splitk(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> B, Cx<R> beta, View<R> C,
+                 Cx<R>* ws, size_t ws_elems);
 // C = alpha op(A) op(B) + beta C on row-major real matrices (op(X) = X^T if tX); ws (ws_elems
 // elements, may be null) lets long-K products split K over CTAs with a fixed-order reduction.
 template <typename R>

@@ -1,20 +1,21 @@
 // Hermitian eigensolver for larger matrices: Householder reduction to a real symmetric
-// tridiagonal T, eigenvalues of T by bisection, eigenvectors of T by inverse iteration
-// (with modified Gram-Schmidt inside clusters of close eigenvalues), and back-transformation
-// of the eigenvectors with the Householder reflectors.
+// tridiagonal T, eigenvalues of T by multisection, eigenvectors of T by inverse iteration on
+// its unreduced blocks, orthonormalisation, and back-transformation with the reflectors.
 //
 // 1. hetrd_kernel (cooperative, one CTA per SM): for column i the reflector
 //    H_i = I - tau_i v_i v_i^H (v_i[i+1] = 1) maps W[i+1:, i] to (beta, 0, ...), beta real;
 //    p = tau W22 v, w = p - (tau/2)(p^H v) v, W22 -= v w^H + w v^H.  Rows are owned
-//    cyclically by the CTAs; three bounded grid barriers per column (norm ready, p ready,
-//    update done).  T = Q^H A Q with Q = H_0 H_1 ... H_{n-2}; d = diag, e = sub-diagonal.
-// 2. bisect_kernel: eigenvalue j (descending) by bisection on the Sturm count of T.
+//    cyclically by the CTAs; two bounded grid barriers per column (p ready, update done).
+//    T = Q^H A Q with Q = H_0 H_1 ... H_{n-2}; d = diag, e = sub-diagonal.
+// 2. T is split where |e_i| <= 32 eps ||T||; bisect_kernel finds eigenvalue k of each
+//    unreduced block by 33-section of its Sturm count (one warp per eigenvalue).
 // 3. inverse_iter_kernel: one thread per eigenvector; LU with partial pivoting of
-//    (T - lambda_j I), three solves from a seeded start vector, normalised.
-// 4. cluster_mgs_kernel: one CTA per cluster of eigenvalues closer than ortol; modified
-//    Gram-Schmidt of its vectors in order.
-// 5. backtransform_kernel: one thread per column of Z applies H_{n-2} .. H_0 (X = Q Z).
-// Every grid barrier spins a bounded number of times; on timeout it records an error word.
+//    (T_b - lambda I) on the eigenvalue's block, three solves from a seeded start vector.
+// 4. cluster_mgs_kernel: one CTA per cluster of close eigenvalues of one block;
+//    Gram-Schmidt (twice) of its vectors in order.
+// 5. All eigenvectors of T are made orthonormal (block Gram-Schmidt twice, Cholesky-QR
+//    twice, on real GEMMs), then X = Q Z is formed with compact-WY panels of 32 reflectors.
+// Every grid barrier waits a bounded time; on timeout it records an error word.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
       scale = cmake<R>((R)(dr / den), (R)(-di / den));
     }
     const Cx<R> tv = cmake<R>((R)tr, (R)ti);
+#pragma unroll 4
     for (int j = i + 1 + t; j < n; j += nt) vs[j] = j == i + 1 ? cmake<R>(1, 0) : scale * W[(long long)j * n + i];
     if (c == 0 && t == 0) {
       d[i] = W[(long long)i * n + i].x;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
       for (int r = r0 + warp * G; r < n; r += nw * G) {
         Cx<R> sacc = cmake<R>(0, 0);
         const Cx<R>* row = W + (long long)r * n;
-#pragma unroll 4
+#pragma unroll 16
         for (int j = i + 1 + lane; j < n; j += 32) cfma(sacc, row[j], vs[j]);
         double sr = sacc.x, si = sacc.y;
         for (int o = 16; o > 0; o >>= 1) {
@@ -139,19 +141,43 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
     __syncthreads();
     const Cx<R> a2 = cmake<R>((R)(-0.5 * (tr * pr - ti * pi)), (R)(-0.5 * (tr * pi + ti * pr)));
     double nn = 0;
-    for (int r = r0; r < n; r += G) {
-      Cx<R>* row = W + (long long)r * n;
-      const Cx<R> vr = vs[r];
-      const Cx<R> wr = ps[r] + a2 * vr;
-      if (t == 0 && r > i + 1) row[i] = vr;  // Householder vector kept for the back-transformation
-#pragma unroll 4
-      for (int j = i + 1 + t; j < n; j += nt) {
-        const Cx<R> vj = vs[j];
-        const Cx<R> wj = ps[j] + a2 * vj;
-        Cx<R> x = row[j];
-        x = x - vr * conj(wj) - wr * conj(vj);
-        row[j] = x;
-        if (j == i + 1 && r >= i + 3) nn += (double)abs2(x);
+    // owned rows four at a time, four column strides per pass: up to 16 independent loads per thread
+    for (int rb = r0; rb < n; rb += 4 * G) {
+      Cx<R>* rowp[4];
+      Cx<R> vr[4], wr[4];
+      bool ok[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = rb + q * G;
+        ok[q] = r < n;
+        rowp[q] = W + (long long)(ok[q] ? r : rb) * n;
+        vr[q] = ok[q] ? vs[r] : cmake<R>(0, 0);
+        wr[q] = ok[q] ? ps[r] + a2 * vr[q] : cmake<R>(0, 0);
+        if (t == 0 && ok[q] && r > i + 1) rowp[q][i] = vr[q];  // Householder vector for the back-transformation
+      }
+      for (int j0 = i + 1 + t; j0 < n; j0 += 4 * nt) {
+        Cx<R> x[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * nt;
+            if (ok[q] && j < n) x[q][u] = rowp[q][j];
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * nt;
+          if (j >= n) break;
+          const Cx<R> vj = vs[j];
+          const Cx<R> wj = ps[j] + a2 * vj;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (!ok[q]) continue;
+            const Cx<R> y = x[q][u] - vr[q] * conj(wj) - wr[q] * conj(vj);
+            rowp[q][j] = y;
+            if (j == i + 1 && rb + q * G >= i + 3) nn += (double)abs2(y);
+          }
+        }
       }
     }
     if (nn != 0) atomicAdd(&acc[par ^ 1], nn);
@@ -249,13 +275,15 @@ __global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* pe
     Z[i * K + j] = (R)((double)(h & 0xFFFFFF) / 16777216.0 + 0.5);
   }
   for (int iter = 0; iter < 3; ++iter) {
-    // forward: apply L (with the recorded swaps) to z
+    // forward: apply L (with the recorded swaps) to z; the running entry stays in a register
+    R cur = Z[s * K + j];
     for (int i = s; i < t - 1; ++i) {
-      R zi = Z[i * K + j], zn = Z[(i + 1) * K + j];
+      R zi = cur, zn = Z[(i + 1) * K + j];
       if (piv[i * K + j]) { R tmp = zi; zi = zn; zn = tmp; }
       Z[i * K + j] = zi;
-      Z[(i + 1) * K + j] = zn - Lm[i * K + j] * zi;
+      cur = zn - Lm[i * K + j] * zi;
     }
+    Z[(t - 1) * K + j] = cur;
     // backward: U z = y
     R z2 = 0, z1 = 0;
     for (int i = t - 1; i >= s; --i) {
@@ -273,36 +301,50 @@ __global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* pe
   }
 }
 
-// Modified Gram-Schmidt, in order, of the columns cidx[coff[c] .. coff[c+1]) of Z (one cluster of
-// close eigenvalues of one unreduced block per CTA); the vectors live on rows [rlo[c], rhi[c]).
+// Gram-Schmidt, in order, of the columns cidx[coff[c] .. coff[c+1]) (at most 64) of Z: one cluster
+// of close eigenvalues of one unreduced block per CTA; the vectors live on rows [rlo[c], rhi[c]).
+// Each vector is projected twice against all earlier members of its cluster (classical
+// Gram-Schmidt with one re-orthogonalisation: the dot products of one pass are independent and
+// are taken by the warps side by side) and then normalised.
 template <typename R>
 __global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, const int* cidx, const int* coff,
                                                           const int* rlo, const int* rhi) {
-  __shared__ double red[32];
-  const int c0 = coff[blockIdx.x], c1 = coff[blockIdx.x + 1];
+  __shared__ double coef[64];
+  __shared__ double red[8];
+  __shared__ int col[64];
+  const int c0 = coff[blockIdx.x], m = coff[blockIdx.x + 1] - c0;
   const int r0 = rlo[blockIdx.x], r1 = rhi[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long long K = n;
-  auto block_dot = [&](int x, int y) {
-    double s = 0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += (double)Z[r * K + x] * Z[r * K + y];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    double tot = 0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += red[q];
-    return tot;
-  };
-  for (int a = c0; a < c1; ++a) {
-    const int jv = cidx[a];
-    for (int b = c0; b < a; ++b) {
-      const int ip = cidx[b];
-      const double tot = block_dot(ip, jv);
-      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Z[r * K + jv] -= (R)tot * Z[r * K + ip];
+  if (threadIdx.x < m) col[threadIdx.x] = cidx[c0 + threadIdx.x];
+  __syncthreads();
+  for (int a = 0; a < m; ++a) {
+    const int jv = col[a];
+    for (int pass = 0; pass < 2 && a > 0; ++pass) {
+      for (int b = warp; b < a; b += nw) {
+        const int ip = col[b];
+        double sdot = 0;
+        for (int r = r0 + lane; r < r1; r += 32) sdot += (double)Z[r * K + ip] * Z[r * K + jv];
+        for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+        if (lane == 0) coef[b] = sdot;
+      }
+      __syncthreads();
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double v = Z[r * K + jv];
+        for (int b = 0; b < a; ++b) v -= coef[b] * (double)Z[r * K + col[b]];
+        Z[r * K + jv] = (R)v;
+      }
       __syncthreads();
     }
-    const R inv = (R)(1.0 / sqrt(block_dot(jv, jv)));
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Z[r * K + jv] *= inv;
+    double sq = 0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) sq += (double)Z[r * K + jv] * Z[r * K + jv];
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    double tot = 0;
+    for (int q = 0; q < nw; ++q) tot += red[q];
+    const double inv = tot > 0 ? 1.0 / sqrt(tot) : 0.0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Z[r * K + jv] = (R)(Z[r * K + jv] * inv);
     __syncthreads();
   }
 }
@@ -326,18 +368,26 @@ __global__ void panel_kernel(int n, int i0, int nb, const Cx<R>* W, Cx<R>* P) {
 // Compact-WY factor T (nb x nb, upper triangular) of H_{i0} ... H_{i0+nb-1} = I - V T V^H from
 // S = V^H V: T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] S[0:j, j].
 template <typename R>
-__global__ void wy_t_kernel(int nb, const Cx<R>* S, const Cx<R>* tau, Cx<R>* T) {
-  if (threadIdx.x != 0) return;
-  for (int a = 0; a < nb * nb; ++a) T[a] = cmake<R>(0, 0);
+__global__ void __launch_bounds__(32) wy_t_kernel(int nb, const Cx<R>* S, const Cx<R>* tau, Cx<R>* T) {
+  // thread a owns row a of T; column j needs the columns before it, so j runs in order
+  __shared__ Cx<R> Ts[32][33];
+  __shared__ Cx<R> Ss[32][33];
+  const int a = threadIdx.x;
+  for (int j = 0; j < nb; ++j)
+    if (a < nb) { Ss[a][j] = S[a * nb + j]; Ts[a][j] = cmake<R>(0, 0); }
+  __syncwarp();
   for (int j = 0; j < nb; ++j) {
     const Cx<R> tj = tau[j];
-    T[j * nb + j] = tj;
-    for (int a = 0; a < j; ++a) {
-      Cx<R> acc = cmake<R>(0, 0);
-      for (int b = a; b < j; ++b) cfma(acc, T[a * nb + b], S[b * nb + j]);
-      T[a * nb + j] = cmake<R>(R(0), R(0)) - tj * acc;
-    }
+    Cx<R> acc = cmake<R>(0, 0);
+    if (a < j)
+      for (int b = a; b < j; ++b) cfma(acc, Ts[a][b], Ss[b][j]);
+    __syncwarp();
+    if (a < j) Ts[a][j] = cmake<R>(R(0), R(0)) - tj * acc;
+    if (a == j) Ts[j][j] = tj;
+    __syncwarp();
   }
+  for (int j = 0; j < nb; ++j)
+    if (a < nb) T[a * nb + j] = Ts[a][j];
 }
 
 // Real G (nb x nb symmetric positive definite, nb <= 64) = R^T R with R upper triangular
@@ -379,12 +429,27 @@ __global__ void __launch_bounds__(64) chol_inv_kernel(int nb, const R* G, R* Rin
     if (c < nb) Rinv[r * nb + c] = r <= c ? A[c * 65 + r] : R(0);
 }
 
-// dst[r * ldd + c] = src[r * lds + c] for an m x k real block
+// Z[r, 0:nb] <- Z[r, 0:nb] Ti for the rows of one tile of RT rows per CTA (Ti: nb x nb upper
+// triangular, nb <= 64), in place: each CTA reads its rows into shared memory before writing back.
 template <typename R>
-__global__ void copy_real_kernel(int m, int k, const R* src, long long lds, R* dst, long long ldd) {
-  const long long tot = (long long)m * k;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
-    dst[(e / k) * ldd + e % k] = src[(e / k) * lds + e % k];
+__global__ void __launch_bounds__(256) right_mul_inplace_kernel(int m, int nb, R* Z, long long ldz, const R* Ti) {
+  constexpr int RT = sizeof(R) == 8 ? 16 : 64;
+  __shared__ R Zs[RT][65];
+  __shared__ R Ts[64][65];
+  const int r0 = blockIdx.x * RT;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) Ts[e / nb][e % nb] = Ti[e];
+  for (int e = threadIdx.x; e < RT * nb; e += blockDim.x) {
+    const int rr = e / nb, c = e % nb;
+    Zs[rr][c] = r0 + rr < m ? Z[(long long)(r0 + rr) * ldz + c] : R(0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * nb; e += blockDim.x) {
+    const int rr = e / nb, c = e % nb;
+    if (r0 + rr >= m) continue;
+    R acc = 0;
+    for (int k = 0; k <= c; ++k) acc += Zs[rr][k] * Ts[k][c];
+    Z[(long long)(r0 + rr) * ldz + c] = acc;
+  }
 }
 
 template <typename R>
@@ -404,7 +469,8 @@ size_t tri_workspace_bytes(int n, int real_bytes) {
   b += 8 * (size_t)n * c;        // d, e, tau, v, p, w, cluster bounds
   b += 6 * (size_t)n * 8 + 8 * 256;  // block eigenvalues, block bounds, permutation, cluster lists
   b += 3 * 32 * (size_t)n * c + 2 * 32 * 32 * c + 7 * 256;  // WY panel, Y1, Y2, S, T
-  b += (size_t)(8 + 2) * n * 64 * (c / 2) + 2 * 64 * 64 * (c / 2) + 5 * 256;  // real orthonormalisation
+  b += (size_t)(8 + 1) * n * 64 * (c / 2) + 2 * 64 * 64 * (c / 2) + 5 * 256;  // real orthonormalisation
+  b += (size_t)16 * n * 32 * c + 256;                                          // split-K partials
   return b + 64 * 1024;
 }
 
@@ -431,10 +497,11 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   Cx<R>* Tm = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * 32 * 32));
   Cx<R>* Y1 = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)n * 32));
   Cx<R>* Y2 = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)n * 32));
+  const size_t wc_elems = (size_t)16 * n * 32;  // split-K partial products of the WY panels
+  Cx<R>* Wc = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * wc_elems));
   const size_t wr_elems = (size_t)8 * n * 64;
   R* Wr = reinterpret_cast<R*>(take(sizeof(R) * wr_elems));
   R* Cr = reinterpret_cast<R*>(take(sizeof(R) * (size_t)n * 64));
-  R* Yr = reinterpret_cast<R*>(take(sizeof(R) * (size_t)n * 64));
   R* Sr = reinterpret_cast<R*>(take(sizeof(R) * 64 * 64));
   R* Tr = reinterpret_cast<R*>(take(sizeof(R) * 64 * 64));
   R* wf = reinterpret_cast<R*>(take(sizeof(R) * n));
@@ -453,7 +520,7 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   cudaMemsetAsync(d_err, 0, sizeof(int) * 4, st);
   // optional phase timing (MPSGB_TRI_PROFILE=1): event pairs around each phase, printed to stderr
   static const bool prof = std::getenv("MPSGB_TRI_PROFILE") != nullptr;
-  cudaEvent_t pev[6] = {nullptr};
+  cudaEvent_t pev[7] = {nullptr};
   if (prof) for (auto& x : pev) cudaEventCreate(&x);
   if (prof) cudaEventRecord(pev[0], st);
   // ---- 1. tridiagonalisation (cooperative persistent kernel, one CTA per SM)
@@ -586,12 +653,12 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
       for (int pass = 0; pass < 2; ++pass) {
         rgemm<R>(st, nb, nb, n, R(1), Zb, n, true, Zb, n, false, R(0), Sr, nb, Wr, wr_elems);
         chol_inv_kernel<R><<<1, 64, 0, st>>>(nb, Sr, Tr, d_err + 1);
-        rgemm<R>(st, n, nb, nb, R(1), Zb, n, false, Tr, nb, false, R(0), Yr, nb, Wr, wr_elems);
-        copy_real_kernel<R><<<256, 256, 0, st>>>(n, nb, Yr, nb, Zb, n);
-        count_launch();
-        count_launch();
+        right_mul_inplace_kernel<R><<<(n + (sizeof(R) == 8 ? 15 : 63)) / (sizeof(R) == 8 ? 16 : 64), 256, 0, st>>>(
+            n, nb, Zb, n, Tr);
+        count_launch(2);
       }
     }
+    if (prof) cudaEventRecord(pev[6], st);
     real_to_complex_kernel<R><<<1024, 256, 0, st>>>(nn_, Z, X);
     count_launch();
     const Cx<R> one = cmake<R>(1, 0), zero = cmake<R>(0, 0), mone = cmake<R>(-1, 0);
@@ -602,11 +669,13 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
       panel_kernel<R><<<256, 256, 0, st>>>(n, i0, nb, Wm, Pn);
       count_launch();
       // S = V^H V, T from S, Y = V^H X, Y2 = T Y, X -= V Y2
-      gemm<R>(st, nb, nb, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Pn, nb), zero, rowmajor<R>(Sm, nb));
+      gemm_splitk<R>(st, nb, nb, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Pn, nb), zero, rowmajor<R>(Sm, nb),
+                     Wc, wc_elems);
       wy_t_kernel<R><<<1, 32, 0, st>>>(nb, Sm, tau + i0, Tm);
       count_launch();
       Cx<R>* Xs = X + (long long)(i0 + 1) * n;
-      gemm<R>(st, nb, n, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n));
+      gemm_splitk<R>(st, nb, n, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n), Wc,
+                     wc_elems);
       gemm<R>(st, nb, n, nb, one, rowmajor<R>(Tm, nb), rowmajor<R>(Y1, n), zero, rowmajor<R>(Y2, n));
       gemm<R>(st, m, n, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
     }
@@ -615,10 +684,11 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   if (prof) {
     cudaEventRecord(pev[5], st);
     cudaEventSynchronize(pev[5]);
-    float t[5];
+    float t[5], tor = 0;
     for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], pev[i], pev[i + 1]);
-    std::fprintf(stderr, "tridiag n=%d fp%d: hetrd %.2f bisect %.2f inviter %.2f mgs %.2f (clusters %zu) back %.2f ms\n", n,
-                 (int)(8 * sizeof(R)), t[0], t[1], t[2], t[3], ncl, t[4]);
+    cudaEventElapsedTime(&tor, pev[4], pev[6]);
+    std::fprintf(stderr, "tridiag n=%d fp%d: hetrd %.2f bisect %.2f inviter %.2f mgs %.2f (clusters %zu) back %.2f (orthonormalise %.2f) ms\n",
+                 n, (int)(8 * sizeof(R)), t[0], t[1], t[2], t[3], ncl, t[4], tor);
     for (auto& x : pev) cudaEventDestroy(x);
   }
   int cherr = 0;
