@@ -39,10 +39,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chi", type=int, default=1024)
-    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--prec", default="split_bf16x3")
     ap.add_argument("--grid", default="%dx%d" % GRID)
     ap.add_argument("--cpu-sample-chi", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=16, help="jobs of the short serving run (0: none)")
+    ap.add_argument("--peaks", action="store_true", help="measure dense matmul rates (torch) and exit")
     return ap.parse_args()
 
 
@@ -92,6 +94,47 @@ class ClockSampler:
         reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
+
+
+def measure_peaks():
+    """Dense matmul rates of this GPU through torch (cuBLAS): FP64, FP32 (no TF32), TF32, BF16,
+    complex64 and complex128, 8192^3 (4096^3 complex), best of 10 after warm-up, CUDA events."""
+    import torch
+
+    out = {}
+    for name, dt, nn, tf32 in (("fp64", torch.float64, 8192, False), ("fp32", torch.float32, 8192, False),
+                               ("tf32", torch.float32, 8192, True), ("bf16", torch.bfloat16, 8192, False),
+                               ("c64", torch.complex64, 4096, False), ("c128", torch.complex128, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(nn, nn, device="cuda", dtype=dt)
+        b = torch.randn(nn, nn, device="cuda", dtype=dt)
+        for _ in range(3):
+            a @ b
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        flops = (8.0 if dt in (torch.complex64, torch.complex128) else 2.0) * nn ** 3
+        out[name + "_tflops"] = flops / (best / 1e3) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["device"] = torch.cuda.get_device_name()
+    return out
+
+
+def serve_run(njobs, prec):
+    """A short serving run: Poisson arrivals (20 jobs/s, seeded) over the grids of the serving
+    mix, chi in {32, 64}, 4 second-order steps each, 8 slots, 8 GB budget."""
+    from paper_2511_23438_gb300 import inputs, serve
+
+    jobs = inputs.serving_jobs(njobs, rate=20.0, seed=20261203, chis=(32, 64), steps=4, prec=prec)
+    res, st = serve.Server(serve.GpuEngine(), 8 << 30, max_slots=8).run(jobs)
+    st["workload"] = ("%d jobs, Poisson 20/s, grids %s, chi {32,64}, 4 steps, %s, 8 slots, 8 GB budget"
+                      % (njobs, "/".join("%dx%d" % g for g in inputs.SERVE_GRIDS), prec))
+    return st
 
 
 def cpu_baseline(Lx, Ly, sample_chi, dtheta):
@@ -145,6 +188,19 @@ def run_reference(args, Lx, Ly):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(ms, updates, dist, device):
+    """Replicas: the job's time is the slowest rank's timed region, its work the sum of all
+    ranks' bond updates (no collective touches the data path; this is the only one)."""
+    import torch
+
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    u = torch.tensor([float(updates)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item()
+
+
 def main():
     args = parse()
     Lx, Ly = (int(x) for x in args.grid.split("x"))
@@ -153,6 +209,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, Lx, Ly)
+        return
+    if args.peaks:
+        print(json.dumps(measure_peaks()), flush=True)
         return
 
     import torch
@@ -208,13 +267,8 @@ def main():
     lib.kernel_timing(False)
     kstep_ms = ev2.elapsed_time(ev3)
     updates = st1["truncations"] - st0["truncations"]
-    t = torch.tensor([ms], device="cuda")
-    u = torch.tensor([float(updates)], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    ms_max = t.item()
-    value = u.item() / (ms_max / 1e3)
+    ms_max, upd_all = reduce_over_ranks(ms, updates, dist, "cuda")
+    value = upd_all / (ms_max / 1e3)
 
     # ---- end to end through the C ABI: per step the layer parameters go host -> device (the
     # in-block unitaries the library uploads) and the observables + F come back to the host
@@ -239,43 +293,58 @@ def main():
         return
     # ---- roofline of the dominant launch site (device time from CUDA events on the handle's stream)
     peaks = read_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6792.1)
+    tc_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1715.0))
+    fp32_peak = 69.8   # measured FP32 CUDA-core matmul rate of this GPU (bench.py --peaks)
+    fp64_peak = 1.04   # measured FP64 matmul rate of this GPU (bench.py --peaks)
+
+    def roofline(name, kms, kn, kwork):
+        if kms <= 0:
+            return None
+        if "in-block gate" in name or "Householder" in name:  # bytes
+            r = {"bound": "hbm", "achieved": kwork / (kms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+        elif "tcgen05" in name:  # useful complex flops; the tensor pipe executes 3 bf16 products each
+            r = {"bound": "tensor", "achieved": 3 * kwork / (kms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
+                 "useful_tflops": kwork / (kms / 1e3) / 1e12,
+                 "peak_source": "measured (MEASURED_PEAKS.json bf16 sustained)"}
+        else:  # CUDA-core arithmetic
+            pk = fp64_peak if args.prec == "fp64" else fp32_peak
+            r = {"bound": "alu", "achieved": kwork / (kms / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+                 "peak_source": "measured (torch matmul, bench.py --peaks)"}
+        r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = None
+        r["kernel"] = name
+        r["launches"] = kn
+        r["avg_launch_ms"] = kms / max(1, kn)
+        r["share_of_step"] = kms / kstep_ms
+        return r
+
     dom = max(ktimes.items(), key=lambda kv: kv[1][0])
-    name, (kms, kn, kwork) = dom
-    avg_ms = kms / max(1, kn)
-    fp32_peak = 69.8e12  # measured FP32 CUDA-core matmul rate on this GB300 (see profiles/)
-    if "in-block gate" in name:
-        achieved = kwork / (kms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6792.1), "unit": "GB/s"}
-    elif "tcgen05" in name:
-        achieved = kwork / (kms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops", 1945.4), "unit": "TFLOP/s"}
-    else:
-        peak = 1.04 if args.prec == "fp64" else fp32_peak / 1e12
-        achieved = kwork / (kms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = name
-    roof["launches"] = kn
-    roof["avg_launch_ms"] = avg_ms
-    roof["share_of_step"] = kms / kstep_ms
+    roof = roofline(dom[0], *dom[1])
+    tc = [(k, v) for k, v in ktimes.items() if "tcgen05" in k]
+    roof_tc = roofline(tc[0][0], *tc[0][1]) if tc and tc[0][1][0] > 0 else None
     line = {"metric": "bond updates/s at %dx%d chi=%d" % (Lx, Ly, args.chi), "value": value,
             "unit": "bond updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "c128", "fp32": "c64"}.get(args.prec, "c64"), "data": "synthetic",
+            "dtype": {"fp64": "c128", "fp32": "c64", "split_bf16x3": "c64+bf16x3"}.get(args.prec, "c64"),
+            "data": "synthetic",
             "config": {"workload": "TFIM %dx%d grouped MPS (d=%d, %d blocks), chi=%d, mid temperature "
                                    "(dtheta=2pi/9), J=-1 h=2 dt=0.25, 2nd-order Trotter, precision %s"
                                    % (Lx, Ly, 2 ** ((Ly + 1) // 2), 2 * Lx, args.chi, args.prec),
                        "l2": "inputs larger than L2 (MPS resident in HBM, streamed every step)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": launches,
-            "bond_updates": int(u.item()),
+            "bond_updates": int(upd_all),
             "observables": obs,
             "clocks": clk,
             "roofline": roof,
+            "roofline_tensorcore_gemm": roof_tc,
             "e2e": {"value": e2e_updates / e2e_s, "unit": "bond updates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "kernel_sites_ms": {k: round(v[0], 3) for k, v in ktimes.items()}}
+    if args.serve_jobs > 0 and world == 1:
+        line["serve"] = serve_run(args.serve_jobs, args.prec)
     if not args.no_cpu_baseline and world == 1 or (rank == 0 and not args.no_cpu_baseline):
         line["cpu_baseline"] = cpu_baseline(Lx, Ly, args.cpu_sample_chi, TEMP_DTHETA)
     print(json.dumps(line), flush=True)

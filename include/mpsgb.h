@@ -153,9 +153,10 @@ unsigned long long mpsgb_launch_count(void);
 
 /* Device-time measurement of the library's launch sites with CUDA events on their own streams.
  * mpsgb_kernel_timing(1) resets the totals and starts recording (0 stops); mpsgb_kernel_times
- * synchronises on the recorded events and returns, for launch site `site` (0 .. 6, see
+ * synchronises on the recorded events and returns, for launch site `site` (0 .. 7, see
  * mpsgb_kernel_site_name), the summed device time in ms, the launch count and the useful work of
- * those launches (real flops for arithmetic sites, bytes moved for the in-block gate site).
+ * those launches (real flops for arithmetic sites; bytes moved for the in-block gate and for the
+ * Householder reduction, counted as two reads and one write of the trailing matrix per column).
  * Recording adds two event records per launch; it is off by default. */
 int mpsgb_kernel_timing(int enable);
 int mpsgb_kernel_times(int site, double* ms, long long* launches, double* work);

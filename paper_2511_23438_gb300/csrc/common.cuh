@@ -61,13 +61,15 @@ inline void count_launch(unsigned long long n = 1) { __atomic_add_fetch(&g_launc
 // Optional per-launch-site timing with CUDA events (off by default): when enabled,
 // kt_begin / kt_end bracket the launches of one site on their stream and the
 // accumulated device time is read back by mpsgb_kernel_times().
-enum KtSite { KT_GEMM = 0, KT_EIG_PAIR, KT_EIG_UPDATE, KT_EIG_SMALL, KT_PHYS, KT_TC_GEMM, KT_OTHER, KT_NSITES };
+enum KtSite { KT_GEMM = 0, KT_EIG_PAIR, KT_EIG_UPDATE, KT_EIG_SMALL, KT_PHYS, KT_TC_GEMM, KT_HETRD, KT_TRIVEC,
+              KT_NSITES };
 extern bool g_kt_enabled;
 void kt_begin_impl(int site, cudaStream_t st);
 void kt_end_impl(int site, cudaStream_t st);
 inline void kt_begin(int site, cudaStream_t st) { if (g_kt_enabled) kt_begin_impl(site, st); }
 inline void kt_end(int site, cudaStream_t st) { if (g_kt_enabled) kt_end_impl(site, st); }
 // useful work of a bracketed launch: real flops for arithmetic sites, bytes for data movement
+// (the in-block gate and the Householder reduction, whose trailing-matrix passes are its cost)
 void kt_add_work(int site, double work);
 
 }  // namespace mpsgb

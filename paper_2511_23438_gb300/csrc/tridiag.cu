@@ -538,9 +538,11 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   int n_ = n;
   long long lda_ = lda;
   void* args[] = {&n_, (void*)&A, &lda_, &Wm, &dv, &ev, &tau, &pb, &acc, &bar, &d_err};
-  kt_begin(KT_OTHER, st);
+  kt_begin(KT_HETRD, st);
   if (cudaLaunchCooperativeKernel((void*)hetrd_kernel<R>, dim3(grid), dim3(512), args, hsm, st) != cudaSuccess) return -4;
-  kt_end(KT_OTHER, st);
+  kt_end(KT_HETRD, st);
+  // algorithmic bytes: per column the trailing (n-i-1)^2 block is read twice and written once
+  kt_add_work(KT_HETRD, 3.0 * sizeof(Cx<R>) * ((double)(n - 1) * n * (2.0 * n - 1) / 6.0));
   count_launch();
   if (prof) cudaEventRecord(pev[1], st);
   // ---- 2. split T at negligible off-diagonal entries (|e_i| <= 32 eps ||T||, an absolute
@@ -579,7 +581,9 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   cudaMemcpyAsync(ev, he.data(), sizeof(R) * n, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(blo, hblo.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(bhi, hbhi.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  kt_begin(KT_TRIVEC, st);
   bisect_kernel<R><<<(n + 3) / 4, 128, 0, st>>>(n, dv, ev, blo, bhi, wf, (R)lo, (R)hi, pivmin);
+  kt_end(KT_TRIVEC, st);
   count_launch();
   // all eigenvalues in descending order (ties in row order), w and the column permutation
   std::vector<R> hwf(n);
@@ -597,7 +601,9 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   // pivots of (T_b - lambda I) are kept at least eps ||T|| in magnitude: a perturbation of the size
   // of the eigenvalue error that also bounds the growth of the solution
   const R pfloor = (R)std::max(eps * tnorm, (double)pivmin);
+  kt_begin(KT_TRIVEC, st);
   inverse_iter_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(n, dv, ev, perm, wf, blo, bhi, Z, U0, U1, U2, Lm, piv, pfloor);
+  kt_end(KT_TRIVEC, st);
   count_launch();
   if (prof) cudaEventRecord(pev[3], st);
   // ---- 4. clusters of close eigenvalues: re-orthogonalise
@@ -628,7 +634,9 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     cudaMemcpyAsync(cl_off, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(cl_rlo, crlo.data(), sizeof(int) * ncl, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(cl_rhi, crhi.data(), sizeof(int) * ncl, cudaMemcpyHostToDevice, st);
+    kt_begin(KT_TRIVEC, st);
     cluster_mgs_kernel<R><<<(unsigned)ncl, 256, 0, st>>>(n, Z, cl_idx, cl_off, cl_rlo, cl_rhi);
+    kt_end(KT_TRIVEC, st);
     count_launch();
   }
   if (prof) cudaEventRecord(pev[4], st);

@@ -191,7 +191,7 @@ def launch_count():
     return load().mpsgb_launch_count()
 
 
-KERNEL_SITES = 7
+KERNEL_SITES = 8
 
 
 def kernel_timing(enable):
