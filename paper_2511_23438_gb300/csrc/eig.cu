@@ -413,9 +413,6 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
   if (n <= 0 || batch <= 0) return 0;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
-  double* fro = reinterpret_cast<double*>(take(sizeof(double) * batch));
-  fro2_kernel<R><<<batch, 256, 0, st>>>(n, A, lda, sA, fro);
-  count_launch();
   if (n >= kTridiagMinN) {  // Householder tridiagonal route, one problem at a time
     for (int b = 0; b < batch; ++b) {
       int r = eigh_tridiag<R>(st, n, A + b * sA, lda, w + b * sw, V + b * sV, ldv, ws);
@@ -423,6 +420,10 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
     }
     return 1;
   }
+  // Jacobi routes: squared Frobenius norms set the convergence tolerances
+  double* fro = reinterpret_cast<double*>(take(sizeof(double) * batch));
+  fro2_kernel<R><<<batch, 256, 0, st>>>(n, A, lda, sA, fro);
+  count_launch();
   if (n <= 32) {
     kt_begin(KT_EIG_SMALL, st);
     eig_small_kernel<R><<<batch, 32, 0, st>>>(n, A, lda, sA, w, sw, V, ldv, sV, fro);

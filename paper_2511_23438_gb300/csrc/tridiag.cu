@@ -303,11 +303,12 @@ __global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* pe
 
 // Gram-Schmidt, in order, of the columns cidx[coff[c] .. coff[c+1]) (at most 64) of Z: one cluster
 // of close eigenvalues of one unreduced block per CTA; the vectors live on rows [rlo[c], rhi[c]).
-// Each vector is projected twice against all earlier members of its cluster (classical
-// Gram-Schmidt with one re-orthogonalisation: the dot products of one pass are independent and
-// are taken by the warps side by side) and then normalised.
+// The cluster's vectors are first gathered into ZT (transposed scratch, one contiguous row per
+// vector) so that every later pass reads consecutive words; each vector is projected twice
+// against all earlier members (classical Gram-Schmidt with one re-orthogonalisation, the dot
+// products of a pass taken side by side by the warps), normalised, and scattered back.
 template <typename R>
-__global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, const int* cidx, const int* coff,
+__global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, R* ZT, const int* cidx, const int* coff,
                                                           const int* rlo, const int* rhi) {
   __shared__ double coef[64];
   __shared__ double red[8];
@@ -318,34 +319,45 @@ __global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, const int
   const long long K = n;
   if (threadIdx.x < m) col[threadIdx.x] = cidx[c0 + threadIdx.x];
   __syncthreads();
+  // gather: ZT[col][r] = Z[r][col] (a warp reads the members' entries of one row together)
+  for (int r = r0 + warp; r < r1; r += nw) {
+    if (lane < m) ZT[col[lane] * K + r] = Z[r * K + col[lane]];
+    if (lane + 32 < m) ZT[col[lane + 32] * K + r] = Z[r * K + col[lane + 32]];
+  }
+  __syncthreads();
   for (int a = 0; a < m; ++a) {
-    const int jv = col[a];
+    R* x = ZT + col[a] * K;
     for (int pass = 0; pass < 2 && a > 0; ++pass) {
       for (int b = warp; b < a; b += nw) {
-        const int ip = col[b];
+        const R* y = ZT + col[b] * K;
         double sdot = 0;
-        for (int r = r0 + lane; r < r1; r += 32) sdot += (double)Z[r * K + ip] * Z[r * K + jv];
+        for (int r = r0 + lane; r < r1; r += 32) sdot += (double)y[r] * x[r];
         for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
         if (lane == 0) coef[b] = sdot;
       }
       __syncthreads();
       for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double v = Z[r * K + jv];
-        for (int b = 0; b < a; ++b) v -= coef[b] * (double)Z[r * K + col[b]];
-        Z[r * K + jv] = (R)v;
+        double v = x[r];
+        for (int b = 0; b < a; ++b) v -= coef[b] * (double)ZT[col[b] * K + r];
+        x[r] = (R)v;
       }
       __syncthreads();
     }
     double sq = 0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) sq += (double)Z[r * K + jv] * Z[r * K + jv];
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) sq += (double)x[r] * x[r];
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if (lane == 0) red[warp] = sq;
     __syncthreads();
     double tot = 0;
     for (int q = 0; q < nw; ++q) tot += red[q];
     const double inv = tot > 0 ? 1.0 / sqrt(tot) : 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) Z[r * K + jv] = (R)(Z[r * K + jv] * inv);
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) x[r] = (R)(x[r] * inv);
     __syncthreads();
+  }
+  // scatter back
+  for (int r = r0 + warp; r < r1; r += nw) {
+    if (lane < m) Z[r * K + col[lane]] = ZT[col[lane] * K + r];
+    if (lane + 32 < m) Z[r * K + col[lane + 32]] = ZT[col[lane + 32] * K + r];
   }
 }
 
@@ -391,42 +403,54 @@ __global__ void __launch_bounds__(32) wy_t_kernel(int nb, const Cx<R>* S, const 
 }
 
 // Real G (nb x nb symmetric positive definite, nb <= 64) = R^T R with R upper triangular
-// (right-looking Cholesky, thread c owns column c); writes R^{-1} (nb x nb, row-major).  One shared
-// array: R's strict upper part above the diagonal, R^{-1} transposed on and below it, diag(R) apart.
-// A non-positive pivot sets err and is clamped.
+// (right-looking Cholesky, the trailing update spread over all threads), then R^{-1} by a
+// column sweep from the last row (R X = I: row k of X is fixed, then removed from the rows
+// above), writes R^{-1} (nb x nb, row-major).  A non-positive pivot sets err and is clamped.
+// Dynamic shared memory: two 64 x 65 arrays of R.
 template <typename R>
-__global__ void __launch_bounds__(64) chol_inv_kernel(int nb, const R* G, R* Rinv, int* err) {
-  __shared__ R A[64 * 65];
-  __shared__ R dR[64];
-  const int c = threadIdx.x;
-  for (int r = 0; r < nb; ++r)
-    if (c < nb) A[r * 65 + c] = G[r * nb + c];
+__global__ void __launch_bounds__(256) chol_inv_kernel(int nb, const R* G, R* Rinv, int* err) {
+  extern __shared__ __align__(16) unsigned char ci_smem[];
+  R(*A)[65] = reinterpret_cast<R(*)[65]>(ci_smem);
+  R(*X)[65] = reinterpret_cast<R(*)[65]>(ci_smem + sizeof(R) * 64 * 65);
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < nb * nb; e += nt) {
+    const int r = e / nb, c = e % nb;
+    A[r][c] = G[e];
+    X[r][c] = r == c ? R(1) : R(0);
+  }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    R piv = A[j * 65 + j];
+    R piv = A[j][j];
     if (!(piv > R(0))) {
-      if (c == 0) atomicExch(err, 2);
+      if (t == 0) atomicExch(err, 2);
       piv = sizeof(R) == 8 ? R(1e-300) : R(1e-30);
     }
     const R rjj = sqrt(piv);
     __syncthreads();
-    if (c > j && c < nb) A[j * 65 + c] /= rjj;
-    if (c == j) dR[j] = rjj;
+    for (int c = j + 1 + t; c < nb; c += nt) A[j][c] /= rjj;
+    if (t == 0) A[j][j] = rjj;
     __syncthreads();
-    if (c > j && c < nb)
-      for (int r = j + 1; r <= c; ++r) A[r * 65 + c] -= A[j * 65 + r] * A[j * 65 + c];
-    __syncthreads();
-  }
-  if (c < nb) {  // column c of R^{-1} by back substitution, stored as row c of the lower part
-    for (int r = c; r >= 0; --r) {
-      R v = r == c ? R(1) : R(0);
-      for (int k = r + 1; k <= c; ++k) v -= A[r * 65 + k] * A[c * 65 + k];
-      A[c * 65 + r] = v / dR[r];
+    const int m = nb - j - 1;
+    for (int e = t; e < m * m; e += nt) {
+      const int r = j + 1 + e / m, c = j + 1 + e % m;
+      if (c >= r) A[r][c] -= A[j][r] * A[j][c];
     }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int r = 0; r < nb; ++r)
-    if (c < nb) Rinv[r * nb + c] = r <= c ? A[c * 65 + r] : R(0);
+  for (int k = nb - 1; k >= 0; --k) {
+    const R inv = R(1) / A[k][k];
+    for (int c = k + t; c < nb; c += nt) X[k][c] *= inv;
+    __syncthreads();
+    for (int e = t; e < k * (nb - k); e += nt) {
+      const int r = e / (nb - k), c = k + e % (nb - k);
+      X[r][c] -= A[r][k] * X[k][c];
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < nb * nb; e += nt) {
+    const int r = e / nb, c = e % nb;
+    Rinv[e] = r <= c ? X[r][c] : R(0);
+  }
 }
 
 // Z[r, 0:nb] <- Z[r, 0:nb] Ti for the rows of one tile of RT rows per CTA (Ti: nb x nb upper
@@ -635,7 +659,7 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     cudaMemcpyAsync(cl_rlo, crlo.data(), sizeof(int) * ncl, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(cl_rhi, crhi.data(), sizeof(int) * ncl, cudaMemcpyHostToDevice, st);
     kt_begin(KT_TRIVEC, st);
-    cluster_mgs_kernel<R><<<(unsigned)ncl, 256, 0, st>>>(n, Z, cl_idx, cl_off, cl_rlo, cl_rhi);
+    cluster_mgs_kernel<R><<<(unsigned)ncl, 256, 0, st>>>(n, Z, U0, cl_idx, cl_off, cl_rlo, cl_rhi);  // U0: free LU scratch
     kt_end(KT_TRIVEC, st);
     count_launch();
   }
@@ -651,6 +675,9 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     // Gram-Schmidt) and then made orthonormal by Cholesky-QR, also twice.  Inverse iteration
     // leaves the vectors of well-separated eigenvalues orthogonal to working precision, so they
     // are unchanged; the vectors of close eigenvalues are made orthogonal.
+    const int ci_smem = 2 * 64 * 65 * (int)sizeof(R);
+    if (cudaFuncSetAttribute(chol_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem) != cudaSuccess)
+      return -4;
     for (int b0 = 0; b0 < n; b0 += 64) {
       const int nb = std::min(64, n - b0);
       R* Zb = Z + b0;
@@ -660,7 +687,7 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
       }
       for (int pass = 0; pass < 2; ++pass) {
         rgemm<R>(st, nb, nb, n, R(1), Zb, n, true, Zb, n, false, R(0), Sr, nb, Wr, wr_elems);
-        chol_inv_kernel<R><<<1, 64, 0, st>>>(nb, Sr, Tr, d_err + 1);
+        chol_inv_kernel<R><<<1, 256, ci_smem, st>>>(nb, Sr, Tr, d_err + 1);
         right_mul_inplace_kernel<R><<<(n + (sizeof(R) == 8 ? 15 : 63)) / (sizeof(R) == 8 ? 16 : 64), 256, 0, st>>>(
             n, nb, Zb, n, Tr);
         count_launch(2);
