@@ -63,6 +63,7 @@ template <typename R>
 __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long long lda, Cx<R>* W, R* d, R* e,
                                                     Cx<R>* tau, Cx<R>* pb, double* acc, unsigned* bar, int* err) {
   extern __shared__ __align__(16) unsigned char hetrd_smem[];
+  __shared__ double hsc[6];  // tau (re, im), 1 / (alpha - beta) (re, im), a2 (re, im)
   Cx<R>* vs = reinterpret_cast<Cx<R>*>(hetrd_smem);
   Cx<R>* ps = vs + n;
   const int G = gridDim.x, c = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
@@ -77,31 +78,37 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
   grid_sync(bar, (++nbar) * G, err);
   for (int i = 0; i < n - 1; ++i) {
     const int par = i & 1;
-    // ---- A: reflector of column i (same scalars in every CTA), v into shared memory
-    const Cx<R> alpha = W[(long long)(i + 1) * n + i];
-    const double xn2 = acc[par];
-    const double ar = alpha.x, ai = alpha.y;
-    double beta, tr, ti;
-    Cx<R> scale;
-    if (xn2 == 0.0 && ai == 0.0) {
-      beta = ar; tr = 0; ti = 0;
-      scale = cmake<R>(0, 0);
-    } else {
-      const double nrm_all = sqrt(ar * ar + ai * ai + xn2);
-      beta = ar >= 0 ? -nrm_all : nrm_all;
-      tr = (beta - ar) / beta;
-      ti = -ai / beta;
-      const double dr = ar - beta, di = ai, den = dr * dr + di * di;  // scale = 1 / (alpha - beta)
-      scale = cmake<R>((R)(dr / den), (R)(-di / den));
+    // ---- A: reflector of column i (thread 0 of every CTA forms the same scalars in FP64 and
+    // shares them: FP64 divisions and square roots are slow on this part, so they are not
+    // repeated by every thread), v into shared memory
+    if (t == 0) {
+      const Cx<R> alpha = W[(long long)(i + 1) * n + i];
+      const double xn2 = acc[par];
+      const double ar = alpha.x, ai = alpha.y;
+      double beta, tr, ti, sr = 0, si = 0;
+      if (xn2 == 0.0 && ai == 0.0) {
+        beta = ar; tr = 0; ti = 0;
+      } else {
+        const double nrm_all = sqrt(ar * ar + ai * ai + xn2);
+        beta = ar >= 0 ? -nrm_all : nrm_all;
+        tr = (beta - ar) / beta;
+        ti = -ai / beta;
+        const double dr = ar - beta, di = ai, den = dr * dr + di * di;  // scale = 1 / (alpha - beta)
+        sr = dr / den;
+        si = -di / den;
+      }
+      hsc[0] = tr; hsc[1] = ti; hsc[2] = sr; hsc[3] = si;
+      if (c == 0) {
+        d[i] = W[(long long)i * n + i].x;
+        e[i] = (R)beta;
+        tau[i] = cmake<R>((R)tr, (R)ti);
+      }
     }
-    const Cx<R> tv = cmake<R>((R)tr, (R)ti);
+    __syncthreads();
+    const Cx<R> tv = cmake<R>((R)hsc[0], (R)hsc[1]);
+    const Cx<R> scale = cmake<R>((R)hsc[2], (R)hsc[3]);
 #pragma unroll 4
     for (int j = i + 1 + t; j < n; j += nt) vs[j] = j == i + 1 ? cmake<R>(1, 0) : scale * W[(long long)j * n + i];
-    if (c == 0 && t == 0) {
-      d[i] = W[(long long)i * n + i].x;
-      e[i] = (R)beta;
-      tau[i] = tv;
-    }
     __syncthreads();
     const int r0 = i + 1 + ((c - (i + 1)) % G + G) % G;
     {
@@ -111,13 +118,13 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
         const Cx<R>* row = W + (long long)r * n;
 #pragma unroll 16
         for (int j = i + 1 + lane; j < n; j += 32) cfma(sacc, row[j], vs[j]);
-        double sr = sacc.x, si = sacc.y;
+        R sr = sacc.x, si = sacc.y;
         for (int o = 16; o > 0; o >>= 1) {
           sr += __shfl_xor_sync(0xffffffffu, sr, o);
           si += __shfl_xor_sync(0xffffffffu, si, o);
         }
         if (lane == 0) {
-          const Cx<R> pv = tv * cmake<R>((R)sr, (R)si);
+          const Cx<R> pv = tv * cmake<R>(sr, si);
           pb[r] = pv;
           const Cx<R> v = vs[r];
           dre += (double)pv.x * v.x + (double)pv.y * v.y;  // conj(p) v
@@ -132,14 +139,18 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
     grid_sync(bar, (++nbar) * G, err);
     // ---- B: rank-2 update of the owned rows
     for (int j = i + 1 + t; j < n; j += nt) ps[j] = pb[j];
-    const double pr = acc[2 + 2 * par], pi = acc[3 + 2 * par];
-    if (c == 0 && t == 0) {  // buffers of the other parity are free again
-      acc[par] = 0;
-      acc[2 + 2 * (par ^ 1)] = 0;
-      acc[3 + 2 * (par ^ 1)] = 0;
+    if (t == 0) {  // a2 = -tau (p^H v) / 2
+      const double pr = acc[2 + 2 * par], pi = acc[3 + 2 * par], tr = hsc[0], ti = hsc[1];
+      hsc[4] = -0.5 * (tr * pr - ti * pi);
+      hsc[5] = -0.5 * (tr * pi + ti * pr);
+      if (c == 0) {  // buffers of the other parity are free again
+        acc[par] = 0;
+        acc[2 + 2 * (par ^ 1)] = 0;
+        acc[3 + 2 * (par ^ 1)] = 0;
+      }
     }
     __syncthreads();
-    const Cx<R> a2 = cmake<R>((R)(-0.5 * (tr * pr - ti * pi)), (R)(-0.5 * (tr * pi + ti * pr)));
+    const Cx<R> a2 = cmake<R>((R)hsc[4], (R)hsc[5]);
     double nn = 0;
     // owned rows four at a time, four column strides per pass: up to 16 independent loads per thread
     for (int rb = r0; rb < n; rb += 4 * G) {
@@ -292,12 +303,13 @@ __global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* pe
       z2 = z1; z1 = v;
     }
     // normalise (scaled by the largest entry first, so that squares cannot overflow)
-    double mx = 0, sq = 0;
-    for (int i = s; i < t; ++i) mx = fmax(mx, fabs((double)Z[i * K + j]));
-    if (!(mx > 0) || !(mx < 1e300)) mx = 1;
-    for (int i = s; i < t; ++i) { const double z = Z[i * K + j] / mx; sq += z * z; }
-    const double inv = 1.0 / (mx * sqrt(sq));
-    for (int i = s; i < t; ++i) Z[i * K + j] = (R)(Z[i * K + j] * inv);
+    R mx = 0, sq = 0;
+    for (int i = s; i < t; ++i) mx = fmax(mx, fabs(Z[i * K + j]));
+    if (!(mx > R(0)) || isinf(mx)) mx = 1;
+    const R rmx = R(1) / mx;
+    for (int i = s; i < t; ++i) { const R z = Z[i * K + j] * rmx; sq += z * z; }
+    const R inv = rmx / sqrt(sq);
+    for (int i = s; i < t; ++i) Z[i * K + j] *= inv;
   }
 }
 
@@ -310,8 +322,8 @@ __global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* pe
 template <typename R>
 __global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, R* ZT, const int* cidx, const int* coff,
                                                           const int* rlo, const int* rhi) {
-  __shared__ double coef[64];
-  __shared__ double red[8];
+  __shared__ R coef[64];
+  __shared__ R red[8];
   __shared__ int col[64];
   const int c0 = coff[blockIdx.x], m = coff[blockIdx.x + 1] - c0;
   const int r0 = rlo[blockIdx.x], r1 = rhi[blockIdx.x];
@@ -330,28 +342,28 @@ __global__ void __launch_bounds__(256) cluster_mgs_kernel(int n, R* Z, R* ZT, co
     for (int pass = 0; pass < 2 && a > 0; ++pass) {
       for (int b = warp; b < a; b += nw) {
         const R* y = ZT + col[b] * K;
-        double sdot = 0;
-        for (int r = r0 + lane; r < r1; r += 32) sdot += (double)y[r] * x[r];
+        R sdot = 0;
+        for (int r = r0 + lane; r < r1; r += 32) sdot += y[r] * x[r];
         for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
         if (lane == 0) coef[b] = sdot;
       }
       __syncthreads();
       for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double v = x[r];
-        for (int b = 0; b < a; ++b) v -= coef[b] * (double)ZT[col[b] * K + r];
-        x[r] = (R)v;
+        R v = x[r];
+        for (int b = 0; b < a; ++b) v -= coef[b] * ZT[col[b] * K + r];
+        x[r] = v;
       }
       __syncthreads();
     }
-    double sq = 0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) sq += (double)x[r] * x[r];
+    R sq = 0;
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) sq += x[r] * x[r];
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if (lane == 0) red[warp] = sq;
     __syncthreads();
-    double tot = 0;
+    R tot = 0;
     for (int q = 0; q < nw; ++q) tot += red[q];
-    const double inv = tot > 0 ? 1.0 / sqrt(tot) : 0.0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) x[r] = (R)(x[r] * inv);
+    const R inv = tot > R(0) ? R(1) / sqrt(tot) : R(0);
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) x[r] = x[r] * inv;
     __syncthreads();
   }
   // scatter back
