@@ -409,13 +409,13 @@ size_t eigh_workspace_bytes(int n, int batch, int real_bytes) {
 
 template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
-         long long ldv, long long sV, int batch, void* workspace) {
+         long long ldv, long long sV, int batch, void* workspace, int nvec) {
   if (n <= 0 || batch <= 0) return 0;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
   if (n >= kTridiagMinN) {  // Householder tridiagonal route, one problem at a time
     for (int b = 0; b < batch; ++b) {
-      int r = eigh_tridiag<R>(st, n, A + b * sA, lda, w + b * sw, V + b * sV, ldv, ws);
+      int r = eigh_tridiag<R>(st, n, A + b * sA, lda, w + b * sw, V + b * sV, ldv, ws, nvec);
       if (r < 0) return r;
     }
     return 1;
@@ -481,9 +481,9 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
 }
 
 template int eigh<double>(cudaStream_t, int, const z128*, long long, long long, double*, long long, z128*, long long,
-                          long long, int, void*);
+                          long long, int, void*, int);
 template int eigh<float>(cudaStream_t, int, const c64*, long long, long long, float*, long long, c64*, long long,
-                         long long, int, void*);
+                         long long, int, void*, int);
 
 }  // namespace mpsgb
 

@@ -234,8 +234,10 @@ class EngineT : public Engine {
   }
 
   // ---------------------------------------------------------- eigen helper (device in, host eigenvalues out)
-  void eig(int n, C* A, R* w, C* V, void* ws, std::vector<double>& hw) {
-    int sw = eigh<R>(stream, n, A, n, 0, w, 0, V, n, 0, 1, ws);
+  // nvec > 0: only the eigenvectors of the nvec largest eigenvalues are needed (the others are
+  // not computed on the tridiagonal route)
+  void eig(int n, C* A, R* w, C* V, void* ws, std::vector<double>& hw, int nvec = 0) {
+    int sw = eigh<R>(stream, n, A, n, 0, w, 0, V, n, 0, 1, ws, nvec);
     stats.eig_calls++;
     if (sw == -1) throw Fail{MPSGB_ETIMEDOUT, "Jacobi eigensolver did not converge within its sweep limit"};
     if (sw == -2) throw Fail{MPSGB_ETIMEDOUT, "eigensolver: a bounded grid barrier of the reduction timed out"};
@@ -427,7 +429,7 @@ class EngineT : public Engine {
     scale_cols_pow<R>(stream, r2, rG, Gs, rG, Dv, +1);
     gemm<R>(stream, r2, rG, r2, one, rowmajor<R>(E, r2), rowmajor<R>(Gs, rG), zero, rowmajor<R>(T1, rG));
     gemm<R>(stream, rG, rG, r2, one, transposed<R>(Gs, rG, true), rowmajor<R>(T1, rG), zero, rowmajor<R>(H, rG));
-    eig(rG, H, Lam, V, ws, hL);
+    eig(rG, H, Lam, V, ws, hL, std::max(1, std::min(kcap, rG)));  // at most kcap vectors are kept
     total = 0;
     for (double x : hL) total += std::max(x, 0.0);
     k = std::max(1, count_above(hL, tau, kcap));

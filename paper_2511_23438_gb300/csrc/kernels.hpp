@@ -30,15 +30,18 @@ void rgemm(cudaStream_t st, int M, int N, int K, R alpha, const R* A, long long 
 // Returns the number of outer sweeps (1 for the tridiagonal route), or < 0: -1 Jacobi sweep
 // limit hit, -2 a bounded grid barrier of the reduction timed out, -3 the eigenvectors of the
 // tridiagonal matrix could not be orthonormalised (dependent vectors), -4 launch or device error.
+// nvec > 0: all eigenvalues, but on the tridiagonal route only the eigenvectors of the nvec
+// largest (the first nvec columns of V; the other columns are left undefined).
 size_t eigh_workspace_bytes(int n, int batch, int real_bytes);
 // n above which eigh() uses the Householder-tridiagonal solver (tridiag.cu) instead of Jacobi
 constexpr int kTridiagMinN = 65;
 size_t tri_workspace_bytes(int n, int real_bytes);
 template <typename R>
-int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv, void* workspace);
+int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv, void* workspace,
+                 int nvec = 0);
 template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
-         long long ldv, long long sV, int batch, void* workspace);
+         long long ldv, long long sV, int batch, void* workspace, int nvec = 0);
 
 // ---------------------------------------------------------------- tensor-core split GEMM (tcgemm.cu)
 // C = alpha op(A) op(B) + beta C on complex64 views with 2-term BF16 splits on tcgen05

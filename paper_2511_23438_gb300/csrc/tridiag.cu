@@ -246,9 +246,10 @@ __global__ void bisect_kernel(int n, const R* d, const R* e, const int* blo, con
 // threads of a warp access consecutive words.
 template <typename R>
 __global__ void inverse_iter_kernel(int n, const R* d, const R* e, const int* perm, const R* wf, const int* blo,
-                                    const int* bhi, R* Z, R* U0, R* U1, R* U2, R* Lm, unsigned char* piv, R pfloor) {
+                                    const int* bhi, R* Z, R* U0, R* U1, R* U2, R* Lm, unsigned char* piv, R pfloor,
+                                    int nv) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  if (j >= nv) return;
   const int f = perm[j];
   const R lam = wf[f];
   const int s = blo[f], t = bhi[f];
@@ -510,9 +511,12 @@ size_t tri_workspace_bytes(int n, int real_bytes) {
   return b + 64 * 1024;
 }
 
-// Returns 1, -3 if a grid barrier of the reduction timed out, -4 on a CUDA error.
+// Returns 1, -2 if a grid barrier of the reduction timed out, -3 if the eigenvectors could not be
+// orthonormalised, -4 on a CUDA error.  nvec > 0: only the first nvec eigenvectors are formed.
 template <typename R>
-int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv, void* workspace) {
+int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv, void* workspace,
+                 int nvec) {
+  nvec = (nvec <= 0 || nvec > n) ? n : nvec;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
   const size_t nn = (size_t)n * n;
@@ -638,7 +642,8 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   // of the eigenvalue error that also bounds the growth of the solution
   const R pfloor = (R)std::max(eps * tnorm, (double)pivmin);
   kt_begin(KT_TRIVEC, st);
-  inverse_iter_kernel<R><<<(n + 127) / 128, 128, 0, st>>>(n, dv, ev, perm, wf, blo, bhi, Z, U0, U1, U2, Lm, piv, pfloor);
+  inverse_iter_kernel<R><<<(nvec + 127) / 128, 128, 0, st>>>(n, dv, ev, perm, wf, blo, bhi, Z, U0, U1, U2, Lm, piv,
+                                                              pfloor, nvec);
   kt_end(KT_TRIVEC, st);
   count_launch();
   if (prof) cudaEventRecord(pev[3], st);
@@ -648,13 +653,13 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   const double ortol = (sizeof(R) == 8 ? 1e-10 : 1e-6) * std::max(tnorm, 1e-300);
   std::vector<int> cidx, coff(1, 0), crlo, crhi;
   {
-    std::vector<int> order(n);  // sorted positions grouped by block, descending within a block
-    for (int j = 0; j < n; ++j) order[j] = j;
+    std::vector<int> order(nvec);  // computed positions grouped by block, descending within a block
+    for (int j = 0; j < nvec; ++j) order[j] = j;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hblo[hperm[x]] < hblo[hperm[y]]; });
-    for (int q = 0; q < n;) {
+    for (int q = 0; q < nvec;) {
       const int blk = hblo[hperm[order[q]]];
       int q1 = q + 1;
-      while (q1 < n && hblo[hperm[order[q1]]] == blk && (double)hw[order[q1 - 1]] - (double)hw[order[q1]] < ortol) ++q1;
+      while (q1 < nvec && hblo[hperm[order[q1]]] == blk && (double)hw[order[q1 - 1]] - (double)hw[order[q1]] < ortol) ++q1;
       for (int a0 = q; q1 - q > 1 && a0 < q1; a0 += 64) {
         for (int a = a0; a < std::min(q1, a0 + 64); ++a) cidx.push_back(order[a]);
         coff.push_back((int)cidx.size());
@@ -690,8 +695,8 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     const int ci_smem = 2 * 64 * 65 * (int)sizeof(R);
     if (cudaFuncSetAttribute(chol_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem) != cudaSuccess)
       return -4;
-    for (int b0 = 0; b0 < n; b0 += 64) {
-      const int nb = std::min(64, n - b0);
+    for (int b0 = 0; b0 < nvec; b0 += 64) {
+      const int nb = std::min(64, nvec - b0);
       R* Zb = Z + b0;
       for (int pass = 0; pass < 2 && b0 > 0; ++pass) {
         rgemm<R>(st, b0, nb, n, R(1), Z, n, true, Zb, n, false, R(0), Cr, nb, Wr, wr_elems);
@@ -721,12 +726,12 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
       wy_t_kernel<R><<<1, 32, 0, st>>>(nb, Sm, tau + i0, Tm);
       count_launch();
       Cx<R>* Xs = X + (long long)(i0 + 1) * n;
-      gemm_splitk<R>(st, nb, n, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n), Wc,
-                     wc_elems);
-      gemm<R>(st, nb, n, nb, one, rowmajor<R>(Tm, nb), rowmajor<R>(Y1, n), zero, rowmajor<R>(Y2, n));
-      gemm<R>(st, m, n, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
+      gemm_splitk<R>(st, nb, nvec, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n),
+                     Wc, wc_elems);
+      gemm<R>(st, nb, nvec, nb, one, rowmajor<R>(Tm, nb), rowmajor<R>(Y1, n), zero, rowmajor<R>(Y2, n));
+      gemm<R>(st, m, nvec, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
     }
-    copy_view<R, R>(st, n, n, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
+    copy_view<R, R>(st, n, nvec, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
   }
   if (prof) {
     cudaEventRecord(pev[5], st);
@@ -744,7 +749,7 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   return cherr != 0 ? -3 : 1;
 }
 
-template int eigh_tridiag<double>(cudaStream_t, int, const z128*, long long, double*, z128*, long long, void*);
-template int eigh_tridiag<float>(cudaStream_t, int, const c64*, long long, float*, c64*, long long, void*);
+template int eigh_tridiag<double>(cudaStream_t, int, const z128*, long long, double*, z128*, long long, void*, int);
+template int eigh_tridiag<float>(cudaStream_t, int, const c64*, long long, float*, c64*, long long, void*, int);
 
 }  // namespace mpsgb
