@@ -24,9 +24,10 @@ void rgemm(cudaStream_t st, int M, int N, int K, R alpha, const R* A, long long 
 // Hermitian eigendecomposition of `batch` n x n matrices (row-major, leading dim
 // lda, batch stride sA, read only).  Eigenvalues go to w (descending, stride sw),
 // eigenvectors to the columns of V (row-major n x n, leading dim ldv, stride sV):
-// A = V diag(w) V^H.  Cyclic parallel Jacobi: a warp-level solver for n <= 32 and a
-// blocked solver (16-wide blocks, 32 x 32 pair problems solved by warps, tile
-// updates of the full matrix) up to 64, Householder tridiagonalisation (tridiag.cu) above.
+// A = V diag(w) V^H.  n <= 32: warp-level cyclic Jacobi; 33 <= n <= 64: blocked Jacobi
+// (16-wide blocks, 32 x 32 pair problems solved by warps, tile updates of the full matrix);
+// n >= kTridiagMinN: Householder tridiagonalisation, bisection and inverse iteration on the
+// unreduced blocks, orthonormalisation and back-transformation (tridiag.cu).
 // Returns the number of outer sweeps (1 for the tridiagonal route), or < 0: -1 Jacobi sweep
 // limit hit, -2 a bounded grid barrier of the reduction timed out, -3 the eigenvectors of the
 // tridiagonal matrix could not be orthonormalised (dependent vectors), -4 launch or device error.
