@@ -65,7 +65,8 @@ typedef enum { MPSGB_LAYER_X = 0, MPSGB_LAYER_ZZ = 1 } mpsgb_layer;
 typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2 } mpsgb_obs;
 
 typedef struct {
-  int Lx, Ly;          /* grid: Lx rows of Ly qubits, periodic in both directions; 2..16 each, n <= 256 */
+  int Lx, Ly;          /* grid: Lx rows of Ly qubits, periodic in both directions; 2 <= Lx <= 16,
+                          2 <= Ly <= 10 (blocks of at most 2^5 states), Lx * Ly <= 160 */
   int chi_max;         /* maximum bond dimension chi (>= 1) */
   double theta;        /* absolute initial angle of Eq. initial_state (use mpsgb_initial_theta) */
   mpsgb_precision prec;
