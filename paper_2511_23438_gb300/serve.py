@@ -95,7 +95,13 @@ class Server:
                 # admit, in arrival order, what has arrived and fits
                 while pending and pending[0]["arrival"] * time_scale <= now() and len(running) < self.slots:
                     job = pending[0]
-                    fp = self.engine.footprint(job)
+                    try:
+                        fp = self.engine.footprint(job)
+                    except Exception as e:  # an invalid job is reported, the others go on
+                        pending.popleft()
+                        results[job["jid"]] = {"error": "%s: %s" % (type(e).__name__, e),
+                                               "arrival": job["arrival"] * time_scale}
+                        continue
                     if fp > self.budget:
                         pending.popleft()
                         results[job["jid"]] = {"error": "footprint %d B exceeds the budget %d B" % (fp, self.budget),

@@ -1,5 +1,6 @@
 """Serving loop host logic (no GPU): admission by footprint budget and slots, arrival order,
 continuous batching, rejection of jobs larger than the budget, latency statistics."""
+import math
 import threading
 import time
 
@@ -79,3 +80,24 @@ def test_one_slot_serialises():
     eng = FakeEngine()
     res, st = serve.Server(eng, 1 << 40, max_slots=1).run(_jobs()[:6])
     assert eng.max_active == 1 and st["completed"] == 6
+
+
+class PickyEngine(FakeEngine):
+    def footprint(self, job):
+        if job["Lx"] > 16:
+            raise ValueError("grid must have Lx <= 16")
+        return super().footprint(job)
+
+
+def test_invalid_job_is_reported_and_the_rest_served():
+    jobs = _jobs()[:5]
+    jobs.append(dict(jobs[0], jid=50, Lx=40, arrival=0.0005))
+    res, st = serve.Server(PickyEngine(), 1 << 40, max_slots=2).run(jobs)
+    assert "ValueError" in res[50]["error"] and st["completed"] == 5 and st["failed"] == 1
+
+
+def test_batched_mix_is_seeded():
+    a = inputs.batched_mix(64, seed=7)
+    assert a == inputs.batched_mix(64, seed=7) and a != inputs.batched_mix(64, seed=8)
+    assert all(math.pi / 12 <= j["dtheta"] <= math.pi / 3 for j in a)
+    assert {j["chi"] for j in a} <= {32, 64, 128, 256, 512}
