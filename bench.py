@@ -345,7 +345,7 @@ def main():
             "kernel_sites_ms": {k: round(v[0], 3) for k, v in ktimes.items()}}
     if args.serve_jobs > 0 and world == 1:
         line["serve"] = serve_run(args.serve_jobs, args.prec)
-    if not args.no_cpu_baseline and world == 1 or (rank == 0 and not args.no_cpu_baseline):
+    if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(Lx, Ly, args.cpu_sample_chi, TEMP_DTHETA)
     print(json.dumps(line), flush=True)
     if dist:
