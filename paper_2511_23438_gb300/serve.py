@@ -81,7 +81,9 @@ class Server:
         """Serve `jobs` (arrival times scaled by time_scale) to completion.
 
         Returns (results, stats): results[jid] = {Z, Z2, X, F, arrival, admit, done, latency}
-        or {error}; stats has jobs/s, latency p50/p99 (s), bond updates/s, peak memory in use.
+        or {error}; stats has jobs/s over the whole run, the service rate over the time the device
+        had work (the saturated rate when the offered load exceeds capacity), latency and queue
+        wait p50/p99 (s), bond updates/s and the peak budget in use.
         """
         pending = collections.deque(sorted(jobs, key=lambda j: (j["arrival"], j["jid"])))
         running = {}  # future -> (job, footprint, admit time)
@@ -137,11 +139,21 @@ class Server:
         makespan = now()
         ok = [r for r in results.values() if "error" not in r]
         lat = np.array([r["latency"] for r in ok]) if ok else np.zeros(0)
+        wait = np.array([r["admit"] - r["arrival"] for r in ok]) if ok else np.zeros(0)
+        # time with at least one job on the device: the service rate there is the saturated rate
+        busy, end = 0.0, -1.0
+        for a, d in sorted((r["admit"], r["done"]) for r in ok):
+            if d > end:
+                busy += d - max(a, end)
+                end = d
         updates = sum(int(r.get("truncations", 0)) for r in ok)
         stats = {"jobs": len(jobs), "completed": len(ok), "failed": len(results) - len(ok), "makespan_s": makespan,
                  "jobs_per_s": len(ok) / makespan if makespan > 0 else 0.0,
                  "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
                  "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+                 "service_rate_busy_jobs_per_s": len(ok) / busy if busy > 0 else 0.0, "busy_s": busy,
+                 "queue_wait_p50_s": float(np.percentile(wait, 50)) if len(wait) else None,
+                 "queue_wait_p99_s": float(np.percentile(wait, 99)) if len(wait) else None,
                  "bond_updates_per_s": updates / makespan if makespan > 0 else 0.0,
                  "peak_budget_in_use": peak, "budget": self.budget, "slots": self.slots}
         return results, stats

@@ -101,3 +101,12 @@ def test_batched_mix_is_seeded():
     assert a == inputs.batched_mix(64, seed=7) and a != inputs.batched_mix(64, seed=8)
     assert all(math.pi / 12 <= j["dtheta"] <= math.pi / 3 for j in a)
     assert {j["chi"] for j in a} <= {32, 64, 128, 256, 512}
+
+
+def test_busy_time_and_service_rate():
+    eng = FakeEngine()
+    jobs = [dict(j, arrival=0.0) for j in _jobs()[:8]]  # all at once: the device never idles
+    res, st = serve.Server(eng, 1 << 40, max_slots=2).run(jobs)
+    assert st["completed"] == 8 and 0 < st["busy_s"] <= st["makespan_s"] + 1e-9
+    assert st["service_rate_busy_jobs_per_s"] >= st["jobs_per_s"] - 1e-9
+    assert st["queue_wait_p50_s"] <= st["queue_wait_p99_s"] and st["queue_wait_p99_s"] > 0
