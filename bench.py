@@ -295,7 +295,7 @@ def main():
     peaks = read_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6792.1)
     tc_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1715.0))
-    fp32_peak = 69.8   # measured FP32 CUDA-core matmul rate of this GPU (bench.py --peaks)
+    fp32_peak = 69.9   # measured FP32 CUDA-core matmul rate of this GPU (bench.py --peaks)
     fp64_peak = 1.10   # measured FP64 matmul rate of this GPU (bench.py --peaks)
 
     def roofline(name, kms, kn, kwork):
