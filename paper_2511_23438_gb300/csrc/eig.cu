@@ -601,7 +601,9 @@ int eig_selftest(int n, int fp64, int kind, unsigned long long seed, double* out
 // For them the whole workspace of the solver lives in one file-scope device array of fixed size,
 // shared by every call on a device.  Host code never dereferences the array's name (on the host it
 // is only a stand-in symbol): its device address is resolved once per device with
-// cudaGetSymbolAddress and passed to the kernels.
+// cudaGetSymbolAddress and passed to the kernels.  The cached address belongs to the device's
+// primary context; it does not survive cudaDeviceReset, after which the library must not be
+// called again in the same process.
 // ---------------------------------------------------------------------------------------------
 namespace mpsgb {
 namespace {
@@ -618,24 +620,35 @@ void* g_noalloc_base[128] = {nullptr};
 template <typename R>
 int eigh_noalloc_t(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx<R>* V, long long ldv,
                    unsigned char* scratch) {
+  // carve the fixed scratch first and reject what does not fit before anything is launched
   unsigned char* ws = scratch;
   auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };
   double* fro = reinterpret_cast<double*>(take(sizeof(double)));
+  const int np = padded(n), nb = np / 16, npairs = nb / 2;
+  Cx<R>* H = nullptr;
+  Cx<R>* Vw = nullptr;
+  Cx<R>* Qs = nullptr;
+  int* perm = nullptr;
+  int* flag = nullptr;
+  int* ident = nullptr;
+  if (n > 32) {
+    H = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)np * np));
+    Vw = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)np * np));
+    Qs = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)npairs * 1024));
+    perm = reinterpret_cast<int*>(take(sizeof(int) * (size_t)np));
+    flag = reinterpret_cast<int*>(take(sizeof(int)));
+    ident = reinterpret_cast<int*>(take(sizeof(int) * (size_t)npairs));
+  }
+  if ((size_t)(ws - scratch) > kNoAllocBytes) return -1;
   fro2_kernel<R><<<1, 256, 0, st>>>(n, A, lda, 0, fro);
   count_launch();
   if (n <= 32) {
     eig_small_kernel<R><<<1, 32, 0, st>>>(n, A, lda, 0, w, 0, V, ldv, 0, fro);
     count_launch();
-    return cudaGetLastError() == cudaSuccess ? 1 : -4;
+    // the call returns only once its kernels are done with the shared scratch
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return -4;
+    return 1;
   }
-  const int np = padded(n), nb = np / 16, npairs = nb / 2;
-  Cx<R>* H = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)np * np));
-  Cx<R>* Vw = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)np * np));
-  Cx<R>* Qs = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)npairs * 1024));
-  int* perm = reinterpret_cast<int*>(take(sizeof(int) * (size_t)np));
-  int* flag = reinterpret_cast<int*>(take(sizeof(int)));
-  int* ident = reinterpret_cast<int*>(take(sizeof(int) * (size_t)npairs));
-  if ((size_t)(ws - scratch) > kNoAllocBytes) return -1;
   {
     long long tot = (long long)np * np;
     blk_init_kernel<R><<<dim3((unsigned)((tot + 255) / 256), 1), 256, 0, st>>>(n, np, A, lda, 0, H, Vw);
@@ -643,7 +656,7 @@ int eigh_noalloc_t(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, 
   }
   int sweeps = -1;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return -4;
     for (int r = 0; r < nb - 1; ++r) {
       blk_pair_kernel<R><<<dim3(npairs, 1), 128, 0, st>>>(np, nb, r, H, Qs, flag, ident, fro);
       blk_update_kernel<R><<<dim3(npairs * npairs + npairs * (np / 32), 1), 256, 0, st>>>(np, nb, r, H, Vw, Qs, ident);
@@ -656,7 +669,8 @@ int eigh_noalloc_t(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, 
   }
   blk_finish_kernel<R><<<1, 1024, sizeof(R) * (size_t)n, st>>>(n, np, H, Vw, w, 0, V, ldv, 0, perm);
   count_launch();
-  if (cudaGetLastError() != cudaSuccess) return -4;
+  // the call returns only once its kernels are done with the shared scratch
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return -4;
   return sweeps < 0 ? -3 : sweeps;
 }
 }  // namespace
