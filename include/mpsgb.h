@@ -97,6 +97,13 @@ int mpsgb_create(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* cu
  * truncation fidelity.  Errors: EINVAL (NaN angle / bad layer), EDEVICE. */
 int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle);
 
+/* Apply only the inter-block gates first .. first+count-1 of the ZZ layer's schedule (the order of
+ * mpsgb_schedule_gates), each exp(-i phi Z_i Z_j) as a rank-2 MPO followed by the truncation of every
+ * bond it spans (Sec. III); in-block phases are not applied.  A ZZ layer is the in-block phases
+ * followed by all gates of the schedule.  For checks of single bond updates and for timing them.
+ * Errors: EINVAL for a range outside the schedule or a NaN angle, EDEVICE, ETIMEDOUT. */
+int mpsgb_apply_gates(mpsgb_handle h, int first, int count, double phi);
+
 /* nsteps Trotter steps: order 2 = X(h dt/2) ZZ(J dt) X(h dt/2) (Eq. trotter_step), order 1 =
  * X(h dt) then ZZ(J dt).  Equivalent to the corresponding apply_layer calls. */
 int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order, int nsteps);
@@ -149,15 +156,24 @@ const char* mpsgb_last_error(void);
  * out[3] eigensolver calls, out[4] eigensolver sweeps.  Host pointer, 5 entries. */
 int mpsgb_stats(mpsgb_handle h, long long out[5]);
 
+/* Cycle limit (SM clock cycles) of the library's bounded device waits on other CTAs: the grid
+ * barriers of the Householder reduction.  A wait that runs out records an error word and lets the
+ * kernel finish; the call then returns MPSGB_ETIMEDOUT and the CUDA context stays usable.  The
+ * default, 4e9 cycles (about 2 s), is far above any legitimate wait; tests lower it to exercise the
+ * timeout path.  cycles <= 0 restores the default.  Process-wide; returns the previous limit.
+ * Not from the paper: a robustness control of this library. */
+long long mpsgb_set_wait_limit(long long cycles);
+
 /* Number of CUDA kernels the library has launched in this process (all handles). */
 unsigned long long mpsgb_launch_count(void);
 
 /* Device-time measurement of the library's launch sites with CUDA events on their own streams.
  * mpsgb_kernel_timing(1) resets the totals and starts recording (0 stops); mpsgb_kernel_times
- * synchronises on the recorded events and returns, for launch site `site` (0 .. 7, see
+ * synchronises on the recorded events and returns, for launch site `site` (0 .. 8, see
  * mpsgb_kernel_site_name), the summed device time in ms, the launch count and the useful work of
- * those launches (real flops for arithmetic sites; bytes moved for the in-block gate and for the
- * Householder reduction, counted as two reads and one write of the trailing matrix per column).
+ * those launches (real flops for arithmetic sites -- 16 n^3 / 3 for the Householder reduction of an
+ * n x n Hermitian matrix; bytes moved for the in-block gate; 0 for the Jacobi SVD, whose work
+ * depends on the data).
  * Recording adds two event records per launch; it is off by default. */
 int mpsgb_kernel_timing(int enable);
 int mpsgb_kernel_times(int site, double* ms, long long* launches, double* work);
@@ -178,19 +194,30 @@ int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long see
  * columns, out[4] 1 if w is descending, out[5] max |w|.  Allocates its own device memory. */
 int mpsgb_eig_selftest(int n, int fp64, int kind, unsigned long long seed, double out[6]);
 
+/* Self-test of the one-sided Jacobi SVD of the FP64 form's truncation (no paper counterpart; a kernel
+ * check): X is a host p x q complex matrix (row-major, interleaved re / im doubles; converted to
+ * complex64 if fp64 == 0), decomposed on the GPU as X = U diag(s) Vh.  s: host, p values,
+ * descending.  out[0] sweeps (negative: the solver's error status), out[1] device ms, out[2]
+ * max |U diag(s) Vh - X| / max |X|, out[3] max |U^H U - I|, out[4] max |Vh Vh^H - I| over the rows
+ * above the numerical-rank cut, out[5] that rank.  Allocates its own device memory. */
+int mpsgb_svd_selftest(int p, int q, int fp64, const double* X, double* s, double out[6]);
+
 /* Allocation-free Hermitian eigendecomposition (the paper has no counterpart: this is a service
  * for callers that cannot allocate device memory at the point of the call, e.g. code that runs
  * under a frozen or request-scoped allocator, or a thread that must not enter the CUDA allocator).
  * A: n x n Hermitian matrix on the device, row-major with leading dimension lda, complex128 if
  * fp64 != 0 else complex64 (read only).  w: n eigenvalues, descending (double / float, device).
  * V: eigenvectors as columns, row-major n x n with leading dimension ldv (device); A = V diag(w) V^H.
- * Work is issued on cuda_stream and the call returns after the stream has finished it.
+ * Work is issued on cuda_stream; the call blocks the calling host thread until that stream has
+ * finished it (including the last kernel), so when it returns the shared array is free again.
  * Nothing is allocated: the solver's workspace is one fixed device array of 1 MiB per device, so
- * n is limited to 1..128 (EINVAL beyond).  The first call on a device resolves that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.  Every call on a
- * device shares the array and leaves its contents behind (each call re-initialises what it reads);
- * calls that overlap on the GPU, from several streams or threads, race on it and must be serialised
- * by the caller.  Errors: EINVAL, ETIMEDOUT (sweep limit), EDEVICE. */
+ * n is limited to 1..128 (EINVAL beyond, before anything is launched).  The first call on a device
+ * resolves that array's device address (cudaGetSymbolAddress) and caches it for the process; make
+ * that first call before any stream capture begins.  The cached address does not survive
+ * cudaDeviceReset.  Every call on a device shares the array and leaves its contents behind (each
+ * call re-initialises what it reads); calls that overlap on the GPU, from several host threads at
+ * once, race on it and must be serialised by the caller.  Errors: EINVAL, ETIMEDOUT (sweep
+ * limit), EDEVICE (a launch failed or the stream reported an error). */
 int mpsgb_eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv,
                        void* cuda_stream);
 

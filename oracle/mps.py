@@ -249,6 +249,33 @@ class MPS:
         return s
 
 
+def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0):
+    """Seeded random MPS with every bond at min(chi, bound), in canonical form with the
+    orthogonality centre on block `centre`, unit norm.  Entries are complex normal; with `decay`
+    every block is scaled by exp(-b / decay) along its right bond index b, so that the Schmidt
+    spectra fall off over the bond (a uniformly random state has nearly flat spectra).  The gauge
+    moves are this module's QR / LQ steps.  An input generator for generic states: it computes
+    nothing of the method and has no pin of its own (its outputs are checked for canonical form
+    and norm where they are used)."""
+    rng = np.random.default_rng(seed)
+    m = MPS(Lx, Ly, chi, 0.3)
+    ds = [b["d"] for b in m.layout]
+    bd = [1] + [int(min(chi, b)) for b in layout.bond_bounds(Lx, Ly)] + [1]
+    blocks = []
+    for i in range(len(ds)):
+        shape = (bd[i], ds[i], bd[i + 1])
+        b = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        if decay is not None:
+            b *= np.exp(-np.arange(bd[i + 1]) / decay)[None, None, :]
+        blocks.append(b)
+    m.blocks = blocks
+    m.centre = len(ds) - 1
+    m.move_centre(0)
+    m.blocks[0] /= np.linalg.norm(m.blocks[0])
+    m.move_centre(centre)
+    return m
+
+
 def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False):
     """TEBD run of Eq. trotter_step (order 2) or X-then-ZZ (order 1).
 

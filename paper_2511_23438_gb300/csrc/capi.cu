@@ -84,6 +84,12 @@ int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle) {
   return guarded([&]() -> int { return layer == MPSGB_LAYER_X ? h->e->apply_x(angle) : h->e->apply_zz(angle); });
 }
 
+int mpsgb_apply_gates(mpsgb_handle h, int first, int count, double phi) {
+  if (!h || !h->e) return fail(MPSGB_EINVAL, "null handle");
+  if (!std::isfinite(phi)) return fail(MPSGB_EINVAL, "angle is not finite");
+  return guarded([&]() -> int { return h->e->apply_gates(first, count, phi); });
+}
+
 int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order, int nsteps) {
   if (!h || !h->e) return fail(MPSGB_EINVAL, "null handle");
   if (!std::isfinite(J) || !std::isfinite(hx) || !std::isfinite(dt)) return fail(MPSGB_EINVAL, "parameter is not finite");
@@ -226,6 +232,12 @@ int mpsgb_stats(mpsgb_handle h, long long out[5]) {
   return MPSGB_OK;
 }
 
+long long mpsgb_set_wait_limit(long long cycles) {
+  long long prev = mpsgb::wait_limit_cycles();
+  mpsgb::set_wait_limit_cycles(cycles > 0 ? cycles : 4000000000LL);
+  return prev;
+}
+
 unsigned long long mpsgb_launch_count(void) { return __atomic_load_n(&mpsgb::g_launch_count, __ATOMIC_RELAXED); }
 
 int mpsgb_schedule_info(int Lx, int Ly, long long out[6]) {
@@ -271,6 +283,14 @@ int mpsgb_eig_selftest(int n, int fp64, int kind, unsigned long long seed, doubl
   if (!out || n < 1 || n > 4096 || kind < 0 || kind > 2) return fail(MPSGB_EINVAL, "bad self-test arguments");
   int s = mpsgb::eig_selftest(n, fp64, kind, seed, out);
   if (s != 0) return fail(MPSGB_EDEVICE, "CUDA error in the eigensolver self-test");
+  return MPSGB_OK;
+}
+
+int mpsgb_svd_selftest(int p, int q, int fp64, const double* X, double* s, double out[6]) {
+  if (!X || !s || !out || p < 1 || q < 1 || p > 4096 || (long long)p * q > (1LL << 24))
+    return fail(MPSGB_EINVAL, "bad self-test arguments");
+  const int st = mpsgb::svd_selftest(p, q, fp64, X, s, out);
+  if (st != 0) return fail(MPSGB_EDEVICE, "CUDA error in the SVD self-test");
   return MPSGB_OK;
 }
 

@@ -58,11 +58,17 @@ template <typename R> inline View<R> transposed(Cx<R>* p, long long ld, bool cj)
 extern unsigned long long g_launch_count;
 inline void count_launch(unsigned long long n = 1) { __atomic_add_fetch(&g_launch_count, n, __ATOMIC_RELAXED); }
 
+// Cycle limit of the library's bounded device waits on other CTAs (grid barriers).  The default
+// (4e9 cycles, about 2 s at 2 GHz) is far above any legitimate wait; a test can lower it through
+// mpsgb_set_wait_limit to make a wait run out and exercise the MPSGB_ETIMEDOUT path.
+long long wait_limit_cycles();
+void set_wait_limit_cycles(long long cycles);
+
 // Optional per-launch-site timing with CUDA events (off by default): when enabled,
 // kt_begin / kt_end bracket the launches of one site on their stream and the
 // accumulated device time is read back by mpsgb_kernel_times().
 enum KtSite { KT_GEMM = 0, KT_EIG_PAIR, KT_EIG_UPDATE, KT_EIG_SMALL, KT_PHYS, KT_TC_GEMM, KT_HETRD, KT_TRIVEC,
-              KT_NSITES };
+              KT_SVD, KT_NSITES };
 extern bool g_kt_enabled;
 void kt_begin_impl(int site, cudaStream_t st);
 void kt_end_impl(int site, cudaStream_t st);

@@ -18,6 +18,13 @@
 //     truncation fidelity is f = sum(kept) / sum(all) -- exactly the SVD truncation of the
 //     state across the bond;
 //  3. the carry multiplies the MPO branches of block q, which becomes the new centre.
+// That Gram route (complex64 forms) squares the Schmidt values, so values below about
+// sqrt(eps) s_0 are not resolved.  The FP64 form therefore takes the exact route, the plain
+// definition of Sec. III with no squaring: the MPO cos(phi) I I - i sin(phi) Z_i Z_j is applied
+// to blocks p .. q (spanned bonds doubled), blocks q .. p+1 are made right-isometric, and each
+// spanned bond p .. q-1 in turn is truncated by the SVD of the centre block (one-sided Jacobi on
+// its conjugate transpose, svd.cu), keeping min(chi, numerical rank) values; centre moves and
+// Schmidt spectra use the same SVD.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -146,6 +153,7 @@ class EngineT : public Engine {
   void* tcws = nullptr;   // BF16 operand planes of the tensor-core GEMM
   size_t tcws_bytes = 0;
   int* derr = nullptr;    // device error word of bounded waits in kernels
+  bool exact = false;     // FP64 form: truncation and centre moves by the SVD (one-sided Jacobi)
 
   // Block-sized contraction: tensor cores in the split form (when every dimension is at least
   // 64), FP32 / FP64 CUDA cores otherwise.
@@ -202,8 +210,10 @@ class EngineT : public Engine {
     for (int b = 0; b < L.N; ++b) dmax = std::max(dmax, d(b));
     cap = (long long)chi_eff * chi_eff * dmax;
     tau = sizeof(R) == 8 ? 1e-16 : 1e-12;
+    // exact route: a block carries doubled bonds on both sides while an MPO is applied
+    const long long cap_blk = exact ? 4 * cap : cap;
     for (int b = 0; b <= L.N; ++b) {
-      C* p = (C*)mem.get(sizeof(C) * cap);
+      C* p = (C*)mem.get(sizeof(C) * cap_blk);
       if (!p) throw Fail{MPSGB_ENOMEM, "allocation of block buffers failed"};
       if (b < L.N) blk.push_back(p); else spare = p;
     }
@@ -213,6 +223,12 @@ class EngineT : public Engine {
     size_t obs = sizeof(C) * (4 * cap + 16 * c2);
     size_t eigws = eigh_workspace_bytes((int)n2, 1, (int)sizeof(R));
     ar.size = std::max(phase, obs) + eigws + (64 << 10);
+    if (exact) {
+      // A^H copy, Vh, U, T (<= 4 cap and (2 chi)^2 each) and the SVD's own working copy
+      const size_t svdws = svd_rows_workspace_bytes((int)n2, (int)(4 * cap / n2 + 1), 1, (int)sizeof(R));
+      ar.size = sizeof(C) * (8 * cap + 3 * n2 * n2) + sizeof(double) * 4 * n2 + svdws + (1 << 20);
+      ar.size = std::max(ar.size, obs + (size_t)(64 << 10));
+    }
     ar.base = (char*)mem.get(ar.size);
     dU = (C*)mem.get(sizeof(C) * 32 * 32 * L.N);
     dsc = (double*)mem.get(sizeof(double) * 16);
@@ -330,9 +346,22 @@ class EngineT : public Engine {
     inter_layer(phi);
     return MPSGB_OK;
   }
+  int apply_gates(int first, int count, double phi) override {
+    if (first < 0 || count < 0 || first + count > (int)L.inter.size())
+      throw Fail{MPSGB_EINVAL, "gate range outside the schedule"};
+    last_f_min = 1.0;
+    for (int i = first; i < first + count; ++i) {
+      if (exact) gate_exact(L.inter[i], phi);
+      else gate(L.inter[i], phi);
+    }
+    return MPSGB_OK;
+  }
   void inter_layer(double phi) {
     last_f_min = 1.0;
-    for (auto& g : L.inter) gate(g, phi);
+    for (auto& g : L.inter) {
+      if (exact) gate_exact(g, phi);
+      else gate(g, phi);
+    }
   }
   int step(double J, double hx, double dt, int order, int nsteps) override {
     double alpha = order == 2 ? 0.5 * hx * dt : hx * dt, phi = J * dt;
@@ -342,6 +371,120 @@ class EngineT : public Engine {
       if (order == 2) apply_x(alpha);
     }
     return MPSGB_OK;
+  }
+
+
+  // ---------------------------------------------------------- exact route (FP64 form)
+  // numerical rank of a descending spectrum of a rows x cols matrix: s > s_0 max(rows, cols) eps
+  static int rank_of(const std::vector<double>& s, long long rows, long long cols, int cap_) {
+    if (s.empty() || !(s[0] > 0)) return 0;
+    const double tol = s[0] * (double)std::max(rows, cols) * 2.220446049250313e-16;
+    int c = 0;
+    while (c < (int)s.size() && c < cap_ && s[c] > tol) ++c;
+    return c;
+  }
+  // X (p x q, row-major) = U diag(s) Vh by Jacobi rotations of the rows; Vh (p x q), U (p x p) and
+  // the device copy ds of s are taken from the arena, hs receives s on the host
+  void jsvd(const C* X, int p, int q, C*& Vh, C*& U, double*& ds, std::vector<double>& hs) {
+    Vh = ar.take<C>((size_t)p * q);
+    U = ar.take<C>((size_t)p * p);
+    ds = ar.take<double>(p);
+    const size_t mark = ar.off;
+    void* ws = ar.take<char>(svd_rows_workspace_bytes(p, q, 1, sizeof(R)));
+    if (!Vh || !U || !ds || !ws) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the SVD"};
+    hs.resize(p);
+    const int sw = svd_rows<R>(stream, p, q, X, q, ds, hs.data(), Vh, q, U, p, ws);
+    ar.off = mark;
+    stats.eig_calls++;
+    if (sw == -1) throw Fail{MPSGB_ETIMEDOUT, "Jacobi SVD did not converge within its sweep limit"};
+    if (sw == -2) throw Fail{MPSGB_ETIMEDOUT, "Jacobi SVD: a bounded grid barrier timed out"};
+    if (sw < 0) throw Fail{MPSGB_EDEVICE, "Jacobi SVD: launch or device error"};
+    stats.eig_sweeps += sw;
+  }
+  // SVD of block m as the (left * d) x right matrix A, through X = A^H = U diag(s) Vh, so that
+  // A = Vh^H diag(s) U^H: new left-isometric block Vh[:k]^H; the rest, diag(s_k) * scale * U[:, :k]^H,
+  // multiplies block m+1.  k = min(kcap, numerical rank) (at least 1).  Returns k; kept / total are
+  // the sums of s^2 over the kept / all values.
+  int svd_split_right(int m, int kcap, double scale_pow, double& kept, double& total) {
+    ar.off = 0;
+    const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+    const int l = left(m), dd = d(m), r = dims[m];
+    const long long M = (long long)l * dd;
+    C* Xt = ar.take<C>((size_t)M * r);
+    if (!Xt) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the SVD"};
+    copy_view<R, R>(stream, r, (int)M, transposed<R>(blk[m], r, true), rowmajor<R>(Xt, M));
+    C *Vh, *U;
+    double* ds;
+    std::vector<double> s;
+    jsvd(Xt, r, (int)M, Vh, U, ds, s);
+    const int k = std::max(1, rank_of(s, M, r, kcap));
+    kept = 0;
+    total = 0;
+    for (int i = 0; i < (int)s.size(); ++i) { total += s[i] * s[i]; if (i < k) kept += s[i] * s[i]; }
+    if (!(kept > 0)) throw Fail{MPSGB_ESTATE, "zero state at a truncation"};
+    copy_view<R, R>(stream, (int)M, k, transposed<R>(Vh, M, true), rowmajor<R>(spare, k));
+    std::swap(blk[m], spare);
+    C* T = ar.take<C>((size_t)k * r);
+    if (!T) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the SVD"};
+    copy_view<R, R>(stream, k, r, transposed<R>(U, r, true), rowmajor<R>(T, r));
+    scale_rows<R>(stream, k, r, T, r, ds, std::pow(kept, scale_pow));
+    const int dn = d(m + 1), rn = right(m + 1);
+    gemm<R>(stream, k, dn * rn, r, one, rowmajor<R>(T, r), rowmajor<R>(blk[m + 1], (long long)dn * rn), zero,
+            rowmajor<R>(spare, (long long)dn * rn));
+    std::swap(blk[m + 1], spare);
+    dims[m] = k;
+    check("SVD split");
+    return k;
+  }
+  // SVD of block m as the left x (d * right) matrix B = U diag(s) Vh: block m <- Vh[:k] (right-
+  // isometric), block m-1 <- block m-1 * U[:, :k] diag(s_k); k = numerical rank (the LQ step)
+  void svd_split_left(int m) {
+    ar.off = 0;
+    const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+    const int l = dims[m - 1], dd = d(m), r = right(m);
+    const long long row = (long long)dd * r;
+    C *Vh, *U;
+    double* ds;
+    std::vector<double> s;
+    jsvd(blk[m], l, (int)row, Vh, U, ds, s);
+    const int k = std::max(1, rank_of(s, l, row, l));
+    copy_view<R, R>(stream, k, (int)row, rowmajor<R>(Vh, row), rowmajor<R>(spare, row));
+    std::swap(blk[m], spare);
+    C* T = ar.take<C>((size_t)l * k);
+    if (!T) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the SVD"};
+    copy_view<R, R>(stream, l, k, rowmajor<R>(U, l), rowmajor<R>(T, k));
+    scale_cols<R>(stream, l, k, T, k, ds, 1.0);
+    const int lq = left(m - 1), dq = d(m - 1);
+    gemm<R>(stream, lq * dq, k, l, one, rowmajor<R>(blk[m - 1], l), rowmajor<R>(T, k), zero, rowmajor<R>(spare, k));
+    std::swap(blk[m - 1], spare);
+    dims[m - 1] = k;
+    check("SVD split");
+  }
+  // inter-block gate by the plain definition of Sec. III (see the file header)
+  void gate_exact(const Layout::Gate& g, double phi) {
+    move_centre(g.p);
+    const int p = g.p, q = g.q;
+    const std::vector<int> od = dims;
+    for (int b = p; b <= q; ++b) {
+      const int l = b == 0 ? 1 : od[b - 1], r = b == L.N - 1 ? 1 : od[b];
+      const int mode = b == p ? 0 : (b == q ? 2 : 1);
+      const int shift = b == p ? L.k[p] - 1 - g.ti : (b == q ? L.k[q] - 1 - g.tj : 0);
+      mpo_expand<R>(stream, mode, l, d(b), r, blk[b], spare, phi, shift);
+      std::swap(blk[b], spare);
+    }
+    for (int m = p; m < q; ++m) dims[m] = 2 * od[m];
+    for (int m = q; m > p; --m) svd_split_left(m);  // right-canonical q .. p+1
+    for (int m = p; m < q; ++m) {
+      double kept = 0, total = 0;
+      svd_split_right(m, cap_bond(m), -0.5, kept, total);
+      const double f = kept / total;
+      F *= f;
+      last_f_min = std::min(last_f_min, f);
+      stats.truncations++;
+    }
+    centre = q;
+    stats.gates++;
+    check("gate");
   }
 
   // ---------------------------------------------------------- centre moves (QR / LQ through the Gram)
@@ -402,8 +545,21 @@ class EngineT : public Engine {
     check("move left");
   }
   void move_centre(int target) {
-    while (centre < target) { move_right(centre); ++centre; }
-    while (centre > target) { move_left(centre); --centre; }
+    while (centre < target) {
+      if (exact) {
+        double kept, total;
+        svd_split_right(centre, 1 << 30, 0.0, kept, total);
+        stats.centre_moves++;
+      } else {
+        move_right(centre);
+      }
+      ++centre;
+    }
+    while (centre > target) {
+      if (exact) { svd_split_left(centre); stats.centre_moves++; }
+      else move_left(centre);
+      --centre;
+    }
   }
 
   // ---------------------------------------------------------- truncation core
@@ -574,6 +730,17 @@ class EngineT : public Engine {
     if (chi < 1 || chi > cfg.chi_max) throw Fail{MPSGB_EINVAL, "truncate: chi out of range"};
     move_centre(L.N - 1);
     move_centre(0);  // everything right of block 0 is right-isometric
+    if (exact) {
+      for (int m = 0; m < L.N - 1; ++m) {
+        const int r = dims[m];
+        double kept = 0, total = 0;
+        const int k = svd_split_right(m, std::min(chi, cap_bond(m)), -0.5, kept, total);
+        F *= kept / total;
+        if (k < r) stats.truncations++;
+        centre = m + 1;
+      }
+      return MPSGB_OK;
+    }
     for (int m = 0; m < L.N - 1; ++m) {
       ar.off = 0;
       int l = left(m), dd = d(m), r = dims[m];
@@ -652,6 +819,18 @@ class EngineT : public Engine {
   int singular_values(int bond, std::vector<double>& s) override {
     if (bond < 0 || bond >= L.N - 1) throw Fail{MPSGB_EINVAL, "bond out of range"};
     move_centre(bond);
+    if (exact) {
+      ar.off = 0;
+      const int l = left(bond), dd = d(bond), r = dims[bond];
+      const long long M = (long long)l * dd;
+      C* Xt = ar.take<C>((size_t)M * r);
+      if (!Xt) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the SVD"};
+      copy_view<R, R>(stream, r, (int)M, transposed<R>(blk[bond], r, true), rowmajor<R>(Xt, M));
+      C *Vh, *U;
+      double* ds;
+      jsvd(Xt, r, (int)M, Vh, U, ds, s);
+      return MPSGB_OK;
+    }
     ar.off = 0;
     int l = left(bond), dd = d(bond), r = dims[bond];
     C* G = ar.take<C>((size_t)r * r);
@@ -723,6 +902,7 @@ Engine* make_engine(const mpsgb_config& cfg, const mpsgb_allocator* alloc, cudaS
     if (cfg.prec == MPSGB_FP64) {
       auto* x = new EngineT<double>();
       e = x;
+      x->exact = true;
       x->init(cfg, alloc, st);
     } else if (cfg.prec == MPSGB_FP32 || cfg.prec == MPSGB_SPLIT_BF16X3) {
       auto* x = new EngineT<float>();

@@ -42,6 +42,7 @@ class Engine {
   virtual int apply_x(double alpha) = 0;                       // prod_j exp(-i alpha X_j)
   virtual int apply_zz(double phi) = 0;                        // prod_<ij> exp(-i phi Z_i Z_j) with truncation
   virtual int step(double J, double h, double dt, int order, int nsteps) = 0;
+  virtual int apply_gates(int first, int count, double phi) = 0;  // inter-block gates [first, first+count)
   virtual int truncate(int chi) = 0;
   virtual int observables(double out[4]) = 0;                  // <Z_tot>, <Z_tot^2>, <X_tot>, norm^2
   virtual int singular_values(int bond, std::vector<double>& s) = 0;

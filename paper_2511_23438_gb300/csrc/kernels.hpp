@@ -44,6 +44,31 @@ template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
          long long ldv, long long sV, int batch, void* workspace, int nvec = 0);
 
+// ---------------------------------------------------------------- Jacobi SVD (svd.cu)
+// SVD of `batch` p x q complex matrices X (row-major, leading dim ldx, batch stride sX; read only) by
+// one-sided Jacobi rotations of the rows: X = U diag(s) Vh with s descending (FP64, device s and/or
+// host s_host, either may be null), Vh (p x q, orthonormal rows where s > 0, zero rows where s == 0)
+// and U (p x p, unitary); Vh or U may be null.  Returns the number of sweeps, -1 if the sweep limit
+// was reached, -2 if a bounded grid barrier timed out, -4 for a launch or device error.  Synchronises
+// the stream.
+size_t svd_rows_workspace_bytes(int p, int q, int batch, int real_bytes);
+template <typename R>
+int svd_rows(cudaStream_t st, int p, int q, const Cx<R>* X, long long ldx, double* s, double* s_host, Cx<R>* Vh,
+             long long ldvh, Cx<R>* U, long long ldu, void* workspace, int batch = 1, long long sX = 0,
+             long long sVh = 0, long long sU = 0);
+// Block expanded by the rank-2 MPO cos(phi) I I - i sin(phi) Z_i Z_j (the bond index of the MPO is the
+// slow half of a doubled bond): mode 0 block p (l, d, r) -> (l, d, 2r); mode 1 a block in between
+// (l, d, r) -> (2l, d, 2r), block diagonal; mode 2 block q (l, d, r) -> (2l, d, r).  shift: position
+// of the gate's qubit in the physical index counted from the least significant bit.
+template <typename R>
+void mpo_expand(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* in, Cx<R>* out, double phi, int shift);
+// X[i, :cols] *= c s[i] for i < rows (s: device FP64)
+template <typename R>
+void scale_rows(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c);
+// X[:rows, j] *= c s[j] for j < cols (s: device FP64)
+template <typename R>
+void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c);
+
 // ---------------------------------------------------------------- tensor-core split GEMM (tcgemm.cu)
 // C = alpha op(A) op(B) + beta C on complex64 views with 2-term BF16 splits on tcgen05
 // (FP32 accumulation).  ws: device workspace of tc_gemm_workspace_bytes(M, N, K) bytes;
@@ -53,6 +78,7 @@ size_t tc_gemm_workspace_bytes(long long M, long long N, long long K);
 int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View<float> B, c64 beta, View<float> C,
             void* ws, size_t ws_bytes, int* d_err);
 int eig_selftest(int n, int fp64, int kind, unsigned long long seed, double* out);
+int svd_selftest(int p, int q, int fp64, const double* X, double* s, double* out);
 int eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv, cudaStream_t st);
 int tc_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
 

@@ -8,6 +8,12 @@ namespace mpsgb {
 unsigned long long g_launch_count = 0;
 
 namespace {
+long long g_wait_limit = 4000000000LL;
+}
+long long wait_limit_cycles() { return __atomic_load_n(&g_wait_limit, __ATOMIC_RELAXED); }
+void set_wait_limit_cycles(long long c) { __atomic_store_n(&g_wait_limit, c, __ATOMIC_RELAXED); }
+
+namespace {
 inline int nblocks(long long n, int t) { long long b = (n + t - 1) / t; return (int)(b > 65535LL * 16 ? 65535LL * 16 : b); }
 
 // One thread per (a, b) fibre of the (l, d, r) block: the d values along the

@@ -297,12 +297,11 @@ int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View
   count_launch(2);
   CUtensorMap ta, tb;
   if (!make_map(&ta, pa, M, Kp, TBM) || !make_map(&tb, pb, N, Kp, TBN)) return -2;
-  static bool attr = false;
   const int smem = TSTAGES * STAGE_BYTES + 1024;
-  if (!attr) {
+  static std::once_flag attr_once;  // several host threads (one per handle) may reach this at once
+  std::call_once(attr_once, [smem] {
     cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  });
   dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
   kt_begin(KT_TC_GEMM, st);
   tc_cgemm_kernel<<<grid, 192, smem, st>>>(ta, tb, M, N, Kp / TBK, alpha, beta, C, d_err);

@@ -92,7 +92,8 @@ const char* mpsgb_kernel_site_name(int site) {
   static const char* names[] = {"cgemm (CUDA-core complex GEMM)", "jacobi pair solve", "jacobi rotation update",
                                 "jacobi small (n<=32)", "in-block gate (apply_phys)", "tcgen05 split GEMM",
                                 "Householder tridiagonal reduction (hetrd)",
-                                "tridiagonal eigenvectors (bisection, inverse iteration, cluster GS)"};
+                                "tridiagonal eigenvectors (bisection, inverse iteration, cluster GS)",
+                                "one-sided Jacobi SVD (exact truncation route)"};
   if (site < 0 || site >= mpsgb::KT_NSITES) return "";
   return names[site];
 }

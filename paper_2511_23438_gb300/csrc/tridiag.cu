@@ -32,11 +32,9 @@ namespace mpsgb {
 namespace {
 // Grid-wide barrier on a monotonic arrival counter: CTA thread 0 adds 1 with release semantics
 // and polls with acquire loads until `target` (= barrier index x gridDim.x) is reached.  The
-// wait is bounded by clock64(); on timeout it records err and continues, so the kernel always
-// finishes and the host reports the error.
-constexpr long long BAR_CYCLES = 4000000000LL;
-
-__device__ __forceinline__ void grid_sync(unsigned* count, unsigned target, int* err) {
+// wait is bounded by clock64() (lim cycles, wait_limit_cycles() on the host); on timeout it records
+// err and continues, so the kernel always finishes and the host reports the error.
+__device__ __forceinline__ void grid_sync(unsigned* count, unsigned target, int* err, long long lim) {
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
@@ -45,7 +43,7 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned target, int*
     for (;;) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
       if (v >= target) break;
-      if (clock64() - t0 > BAR_CYCLES) { atomicExch(err, 1); break; }
+      if (clock64() - t0 > lim) { atomicExch(err, 1); break; }
     }
   }
   __syncthreads();
@@ -61,7 +59,8 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned target, int*
 // acc[0..1]: squared norm of column i (parity i & 1); acc[2..5]: p^H v (re, im) by parity.
 template <typename R>
 __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long long lda, Cx<R>* W, R* d, R* e,
-                                                    Cx<R>* tau, Cx<R>* pb, double* acc, unsigned* bar, int* err) {
+                                                    Cx<R>* tau, Cx<R>* pb, double* acc, unsigned* bar, int* err,
+                                                    long long lim) {
   extern __shared__ __align__(16) unsigned char hetrd_smem[];
   __shared__ double hsc[6];  // tau (re, im), 1 / (alpha - beta) (re, im), a2 (re, im)
   Cx<R>* vs = reinterpret_cast<Cx<R>*>(hetrd_smem);
@@ -75,7 +74,7 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
     if (r >= 2 && t == 0) nrm += (double)abs2(A[(long long)r * lda]);
   }
   if (t == 0 && nrm != 0) atomicAdd(&acc[0], nrm);
-  grid_sync(bar, (++nbar) * G, err);
+  grid_sync(bar, (++nbar) * G, err, lim);
   for (int i = 0; i < n - 1; ++i) {
     const int par = i & 1;
     // ---- A: reflector of column i (thread 0 of every CTA forms the same scalars in FP64 and
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
         atomicAdd(&acc[3 + 2 * par], dim);
       }
     }
-    grid_sync(bar, (++nbar) * G, err);
+    grid_sync(bar, (++nbar) * G, err, lim);
     // ---- B: rank-2 update of the owned rows
     for (int j = i + 1 + t; j < n; j += nt) ps[j] = pb[j];
     if (t == 0) {  // a2 = -tau (p^H v) / 2
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
       }
     }
     if (nn != 0) atomicAdd(&acc[par ^ 1], nn);
-    grid_sync(bar, (++nbar) * G, err);
+    grid_sync(bar, (++nbar) * G, err, lim);
   }
   if (c == 0 && t == 0) d[n - 1] = W[(long long)(n - 1) * n + (n - 1)].x;
 }
@@ -558,11 +557,6 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   cudaMemsetAsync(acc, 0, sizeof(double) * 8, st);
   cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, st);
   cudaMemsetAsync(d_err, 0, sizeof(int) * 4, st);
-  // optional phase timing (MPSGB_TRI_PROFILE=1): event pairs around each phase, printed to stderr
-  static const bool prof = std::getenv("MPSGB_TRI_PROFILE") != nullptr;
-  cudaEvent_t pev[7] = {nullptr};
-  if (prof) for (auto& x : pev) cudaEventCreate(&x);
-  if (prof) cudaEventRecord(pev[0], st);
   // ---- 1. tridiagonalisation (cooperative persistent kernel, one CTA per SM)
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
@@ -577,14 +571,14 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   int grid = sms;
   int n_ = n;
   long long lda_ = lda;
-  void* args[] = {&n_, (void*)&A, &lda_, &Wm, &dv, &ev, &tau, &pb, &acc, &bar, &d_err};
+  long long lim = wait_limit_cycles();
+  void* args[] = {&n_, (void*)&A, &lda_, &Wm, &dv, &ev, &tau, &pb, &acc, &bar, &d_err, &lim};
   kt_begin(KT_HETRD, st);
   if (cudaLaunchCooperativeKernel((void*)hetrd_kernel<R>, dim3(grid), dim3(512), args, hsm, st) != cudaSuccess) return -4;
   kt_end(KT_HETRD, st);
-  // algorithmic bytes: per column the trailing (n-i-1)^2 block is read twice and written once
-  kt_add_work(KT_HETRD, 3.0 * sizeof(Cx<R>) * ((double)(n - 1) * n * (2.0 * n - 1) / 6.0));
+  // algorithmic work: the real flops of a complex Hermitian tridiagonal reduction, 16 n^3 / 3
+  kt_add_work(KT_HETRD, 16.0 / 3.0 * (double)n * n * n);
   count_launch();
-  if (prof) cudaEventRecord(pev[1], st);
   // ---- 2. split T at negligible off-diagonal entries (|e_i| <= 32 eps ||T||, an absolute
   // perturbation of the order of the reduction's own backward error); eigenvalues of each
   // unreduced block by bisection (Gershgorin interval from the host copy of T)
@@ -636,7 +630,6 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   for (int j = 0; j < n; ++j) hw[j] = hwf[hperm[j]];
   cudaMemcpyAsync(perm, hperm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(w, hw.data(), sizeof(R) * n, cudaMemcpyHostToDevice, st);
-  if (prof) cudaEventRecord(pev[2], st);
   // ---- 3. eigenvectors of the blocks by inverse iteration
   // pivots of (T_b - lambda I) are kept at least eps ||T|| in magnitude: a perturbation of the size
   // of the eigenvalue error that also bounds the growth of the solution
@@ -646,7 +639,6 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
                                                               pfloor, nvec);
   kt_end(KT_TRIVEC, st);
   count_launch();
-  if (prof) cudaEventRecord(pev[3], st);
   // ---- 4. clusters of close eigenvalues: re-orthogonalise
   // clusters: within one unreduced block, runs of eigenvalues closer than ortol (vectors of
   // different blocks are orthogonal by construction), re-orthogonalised in chunks of at most 64
@@ -680,7 +672,6 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     kt_end(KT_TRIVEC, st);
     count_launch();
   }
-  if (prof) cudaEventRecord(pev[4], st);
   // ---- 5. back-transformation
   {
     // X = Q Z with Q = H_0 ... H_{n-2}, applied block by block from the last one:
@@ -710,8 +701,7 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
         count_launch(2);
       }
     }
-    if (prof) cudaEventRecord(pev[6], st);
-    real_to_complex_kernel<R><<<1024, 256, 0, st>>>(nn_, Z, X);
+      real_to_complex_kernel<R><<<1024, 256, 0, st>>>(nn_, Z, X);
     count_launch();
     const Cx<R> one = cmake<R>(1, 0), zero = cmake<R>(0, 0), mone = cmake<R>(-1, 0);
     const int nref = n - 1;
@@ -732,16 +722,6 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
       gemm<R>(st, m, nvec, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
     }
     copy_view<R, R>(st, n, nvec, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
-  }
-  if (prof) {
-    cudaEventRecord(pev[5], st);
-    cudaEventSynchronize(pev[5]);
-    float t[5], tor = 0;
-    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], pev[i], pev[i + 1]);
-    cudaEventElapsedTime(&tor, pev[4], pev[6]);
-    std::fprintf(stderr, "tridiag n=%d fp%d: hetrd %.2f bisect %.2f inviter %.2f mgs %.2f (clusters %zu) back %.2f (orthonormalise %.2f) ms\n",
-                 n, (int)(8 * sizeof(R)), t[0], t[1], t[2], t[3], ncl, t[4], tor);
-    for (auto& x : pev) cudaEventDestroy(x);
   }
   int cherr = 0;
   cudaMemcpyAsync(&cherr, d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -57,6 +57,7 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int)]),
     "mpsgb_footprint_bytes": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]),
     "mpsgb_batch_step": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mpsgb_apply_gates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
     "mpsgb_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "mpsgb_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(Allocator), ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_void_p)]),
@@ -64,6 +65,7 @@ _SIGS = {
     "mpsgb_last_error": (ctypes.c_char_p, []),
     "mpsgb_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "mpsgb_launch_count": (ctypes.c_ulonglong, []),
+    "mpsgb_set_wait_limit": (ctypes.c_longlong, [ctypes.c_longlong]),
     "mpsgb_schedule_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
     "mpsgb_schedule_gates": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_int)]),
@@ -75,6 +77,8 @@ _SIGS = {
                                               ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]),
     "mpsgb_eig_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
                                           ctypes.POINTER(ctypes.c_double)]),
+    "mpsgb_svd_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mpsgb_eigh_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     "mpsgb_initial_theta": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
@@ -115,6 +119,37 @@ def config(Lx, Ly, chi, theta, prec="fp64", J=-1.0, h=2.0, dt=0.25, order=2, see
     return Config(Lx, Ly, chi, theta, PRECISIONS[prec] if isinstance(prec, str) else prec, route, seed, J, h, dt, order)
 
 
+def convert_checkpoint(src, dst, prec):
+    """Rewrite a checkpoint of mpsgb_save for another precision form (FP64 <-> complex64 forms):
+    the same state, config and counters, blocks stored in the other element type."""
+    import numpy as np
+    import struct
+
+    with open(src, "rb") as fh:
+        raw = fh.read()
+    n_cfg = ctypes.sizeof(Config)
+    if raw[:8] != b"MPSGBv1\0":
+        raise ValueError("not an mpsgb checkpoint: %s" % src)
+    cfg = Config.from_buffer_copy(raw[8:8 + n_cfg])
+    off = 8 + n_cfg
+    elem, nblk, centre, zero = struct.unpack_from("4i", raw, off)
+    off += 16
+    head = raw[off:off + 8 + 40]
+    off += 48
+    dims = struct.unpack_from("%di" % (nblk - 1), raw, off)
+    off += 4 * (nblk - 1)
+    body = np.frombuffer(raw, dtype=np.complex128 if elem == 8 else np.complex64, offset=off)
+    cfg.prec = PRECISIONS[prec] if isinstance(prec, str) else prec
+    out_t = np.complex128 if cfg.prec == FP64 else np.complex64
+    with open(dst, "wb") as fh:
+        fh.write(b"MPSGBv1\0")
+        fh.write(bytes(cfg))
+        fh.write(struct.pack("4i", 8 if out_t == np.complex128 else 4, nblk, centre, zero))
+        fh.write(head)
+        fh.write(struct.pack("%di" % (nblk - 1), *dims))
+        fh.write(body.astype(out_t).tobytes())
+
+
 def torch_allocator():
     """An mpsgb_allocator backed by PyTorch's caching allocator (keep the returned object alive)."""
     import torch
@@ -145,10 +180,29 @@ def eig_selftest(n, fp64=True, seed=1, kind=0):
     return dict(zip(("sweeps", "ms", "residual", "orthogonality", "sorted", "wmax"), list(out)))
 
 
+def svd_selftest(X, fp64=True):
+    """One-sided Jacobi SVD of the host complex matrix X on the GPU: (s, metrics)."""
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.complex128)
+    p, q = X.shape
+    xs = X.view(np.float64).reshape(-1)
+    s = (ctypes.c_double * p)()
+    out = (ctypes.c_double * 6)()
+    _check(load().mpsgb_svd_selftest(p, q, 1 if fp64 else 0, xs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     s, out))
+    return np.array(list(s)), dict(zip(("sweeps", "ms", "residual", "orth_u", "orth_v", "rank"), list(out)))
+
+
 def eigh_noalloc(n, fp64, A_ptr, lda, w_ptr, V_ptr, ldv, stream=0):
     """Hermitian eigendecomposition of a caller-owned device matrix without any allocation
     (device pointers as ints; see mpsgb_eigh_noalloc in include/mpsgb.h)."""
     _check(load().mpsgb_eigh_noalloc(n, 1 if fp64 else 0, A_ptr, lda, w_ptr, V_ptr, ldv, stream))
+
+
+def set_wait_limit(cycles):
+    """Cycle limit of the library's bounded device waits (<= 0 restores the default); returns the
+    previous limit.  See mpsgb_set_wait_limit in include/mpsgb.h."""
+    return load().mpsgb_set_wait_limit(int(cycles))
 
 
 def initial_theta(J, h, dtheta):
@@ -191,7 +245,7 @@ def launch_count():
     return load().mpsgb_launch_count()
 
 
-KERNEL_SITES = 8
+KERNEL_SITES = 9
 
 
 def kernel_timing(enable):
@@ -242,6 +296,9 @@ class MPS:
 
     def apply_layer(self, layer, angle):
         _check(load().mpsgb_apply_layer(self.h, layer, angle))
+
+    def apply_gates(self, first, count, phi):
+        _check(load().mpsgb_apply_gates(self.h, first, count, phi))
 
     def step(self, J, h, dt, order=2, nsteps=1):
         _check(load().mpsgb_step(self.h, J, h, dt, order, nsteps))
