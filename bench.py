@@ -11,7 +11,13 @@ Multi-GPU: replicas only (one independent MPS per rank, no collective on the dat
 path); value = bond updates of all ranks / max over ranks of the timed region.
 
 --impl reference times the CPU oracle (oracle/, NumPy FP64) on the host cores on a
-bounded sample of the same workload and prints the same JSON line.
+bounded sample of the same workload and prints the same JSON line: bond updates at the
+identical shape (6x8, every bond at chi = 1024) on a seeded random canonical MPS, one
+adjacent inter-block gate (one bond update) per step.
+
+Besides the split-precision form (the timed default), the line reports the FP64 form at the
+same shape (a few bond updates of the evolved state, converted to complex128), the serving
+loop on a mix drawn like the serving configuration, and per-site device times.
 """
 import argparse
 import json
@@ -41,9 +47,12 @@ def parse():
     ap.add_argument("--chi", type=int, default=1024)
     ap.add_argument("--prec", default="split_bf16x3")
     ap.add_argument("--grid", default="%dx%d" % GRID)
-    ap.add_argument("--cpu-sample-chi", type=int, default=64)
+    ap.add_argument("--cpu-updates", type=int, default=1, help="oracle bond updates timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-updates", type=int, default=2, help="FP64-form bond updates timed at full shape (0: none)")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs of the short serving run (0: none)")
+    ap.add_argument("--serve-steps", type=int, default=3, help="Trotter steps per serving job")
+    ap.add_argument("--batch-mps", type=int, default=32, help="MPS of the batched-advance leg (0: none)")
     ap.add_argument("--peaks", action="store_true", help="measure dense matmul rates (torch) and exit")
     return ap.parse_args()
 
@@ -125,67 +134,182 @@ def measure_peaks():
     return out
 
 
-def serve_run(njobs, prec):
-    """A short serving run: Poisson arrivals (20 jobs/s, seeded) over the grids of the serving
-    mix, chi in {32, 64}, 4 second-order steps each, 8 slots, 8 GB budget."""
+def serve_run(njobs, steps, prec):
+    """A serving run drawn like the serving configuration: Poisson arrivals (20 jobs/s, seeded),
+    grids uniform over 4x4 / 5x6 / 6x6 / 6x8 / 7x8, chi uniform over {64, 256, 1024}, temperature
+    uniform over low / mid / high, second-order steps; the HBM budget is the device's free memory
+    at the start (less 4 GB of headroom), 8 slots.  Fewer jobs and steps than the configuration's
+    200 x 20 keep the run within the benchmark's minutes."""
+    import torch
     from paper_2511_23438_gb300 import inputs, serve
 
-    jobs = inputs.serving_jobs(njobs, rate=20.0, seed=20261203, chis=(32, 64), steps=4, prec=prec)
-    res, st = serve.Server(serve.GpuEngine(), 8 << 30, max_slots=8).run(jobs)
-    st["workload"] = ("%d jobs, Poisson 20/s, grids %s, chi {32,64}, 4 steps, %s, 8 slots, 8 GB budget"
-                      % (njobs, "/".join("%dx%d" % g for g in inputs.SERVE_GRIDS), prec))
+    free, _ = torch.cuda.mem_get_info()
+    budget = max(1 << 30, free - (4 << 30))
+    jobs = inputs.serving_jobs(njobs, rate=20.0, seed=20261203, chis=(64, 256, 1024), steps=steps, prec=prec)
+    res, st = serve.Server(serve.GpuEngine(), budget, max_slots=8).run(jobs)
+    st["workload"] = ("%d jobs, Poisson 20/s, grids %s, chi {64,256,1024}, temperatures low/mid/high, %d steps "
+                      "each, %s, 8 slots, budget %.1f GB (free HBM less 4 GB)"
+                      % (njobs, "/".join("%dx%d" % g for g in inputs.SERVE_GRIDS), steps, prec, budget / 1e9))
     return st
 
 
-def cpu_baseline(Lx, Ly, sample_chi, dtheta):
-    """The oracle, as it stands, on a bounded sample of the workload: the same grid at a reduced
-    chi; one untimed Trotter step saturates the bonds, the second step (all of its bond updates
-    and the observables) is timed.  The per-update cost grows ~chi^3."""
-    from oracle import layout, model, mps
+# adjacent inter-block gates between the two middle blocks of the chain (every bond around them
+# at chi for chi <= 1024 on the 6x8 grid): the bond updates timed for the oracle and the FP64 form;
+# `inter` is a gate schedule (p, q, ...) in application order
+def middle_adjacent_gates(inter, Lx):
+    mid = Lx - 1
+    return [i for i, g in enumerate(inter) if g[0] == mid and g[1] == mid + 1]
 
-    th = model.initial_theta(dtheta)
-    alpha, phi = model.layer_angles(J, HX, DT, ORDER)
-    intra, inter = layout.schedule(Lx, Ly)
-    m = mps.MPS(Lx, Ly, sample_chi, th)
 
-    def step():
-        m.x_layer(alpha)
-        m.zz_intra(phi, intra)
-        for g in inter:
-            m.zz_inter(g, phi)
-        m.x_layer(alpha)
-        m.observables()
+class OracleSample:
+    """The oracle, as it stands, on bond updates at the benchmark's shape: a seeded random
+    canonical MPS of the same grid with every bond at min(chi, bound) (the shapes the timed steps
+    work on once the bonds have grown), centre on the middle block; each update is one adjacent
+    inter-block gate there (rank-2 MPO, LQ of the right block, SVD of the centre block,
+    truncation to chi), preceded by the gauge move the previous update left behind."""
 
-    step()
-    n0 = len(m.fidelities)
+    def __init__(self, Lx, Ly, chi):
+        from oracle import layout, mps
+
+        t0 = time.perf_counter()
+        self.m = mps.random_canonical(Lx, Ly, chi, seed=20261203, decay=chi / 8.0, centre=Lx - 1)
+        self.gen_s = time.perf_counter() - t0
+        self.inter = layout.schedule(Lx, Ly)[1]
+        self.gates = middle_adjacent_gates(self.inter, Lx)
+        self.i = 0
+        self.Lx, self.Ly, self.chi = Lx, Ly, chi
+
+    def update(self, phi):
+        g = self.inter[self.gates[self.i % len(self.gates)]]
+        self.i += 1
+        n0 = len(self.m.fidelities)
+        t0 = time.perf_counter()
+        self.m.zz_inter(g, phi)
+        return len(self.m.fidelities) - n0, time.perf_counter() - t0
+
+    def describe(self, n, secs):
+        return ("oracle (NumPy FP64, LAPACK QR + SVD): %d bond update(s) at the identical shape -- %dx%d grid, "
+                "every bond at chi=%d, adjacent gate between the middle blocks (LQ of a 2048 x 16384 block, "
+                "SVD of a 16384 x 2048 centre) -- on a seeded random canonical MPS, %.1f s (state generated "
+                "untimed in %.1f s)" % (n, self.Lx, self.Ly, self.chi, secs, self.gen_s))
+
+
+def batched_run(lib, count, prec):
+    """The batched workload: `count` independent MPS drawn like the batched configuration (grids
+    4x4 .. 6x6, chi uniform over {32, ..., 512}, dtheta uniform in [pi/12, pi/3], seeded), each
+    grown by two untimed Trotter steps; then one step of every MPS is timed twice, handle after
+    handle on one host thread and through mpsgb_batch_step (one host thread and stream per handle,
+    overlapping on the device)."""
+    from paper_2511_23438_gb300 import inputs
+
+    mix = inputs.batched_mix(count, seed=20261203, prec=prec)
+    ms = []
+    for j in mix:
+        th = lib.initial_theta(j["J"], j["h"], j["dtheta"])
+        cfg = lib.config(j["Lx"], j["Ly"], j["chi"], th, prec=prec, J=j["J"], h=j["h"], dt=j["dt"], order=j["order"])
+        ms.append(lib.MPS(cfg))
+    lib.batch_step(ms, 2)
+
+    def updates():
+        return sum(m.stats()["truncations"] for m in ms)
+
+    u0 = updates()
     t0 = time.perf_counter()
-    step()
-    dt = time.perf_counter() - t0
-    n_upd = len(m.fidelities) - n0
+    for m in ms:
+        m.step(m.cfg.J, m.cfg.h, m.cfg.dt, m.cfg.trotter_order, 1)
+        m.observables()
+    t_seq = time.perf_counter() - t0
+    u1 = updates()
+    t0 = time.perf_counter()
+    lib.batch_step(ms, 1)
+    for m in ms:
+        m.observables()
+    t_bat = time.perf_counter() - t0
+    u2 = updates()
+    for m in ms:
+        m.close()
+    return {"mps": count, "precision": prec, "sequential_bond_updates_per_s": (u1 - u0) / t_seq,
+            "batched_bond_updates_per_s": (u2 - u1) / t_bat, "sequential_s": t_seq, "batched_s": t_bat,
+            "bond_updates_per_step": u2 - u1,
+            "workload": "%d MPS, grids 4x4..6x6, chi in {32..512}, dtheta in [pi/12, pi/3], two untimed steps, then "
+                        "one timed step per MPS (wall clock, host-synchronised)" % count}
+
+
+def cpu_baseline(Lx, Ly, chi, n_updates):
+    smp = OracleSample(Lx, Ly, chi)
+    phi = J * DT
+    n = 0
+    secs = 0.0
+    for _ in range(max(1, n_updates)):
+        k, t = smp.update(phi)
+        n += k
+        secs += t
     cores = len(os.sched_getaffinity(0))
-    return {"value": n_upd / dt, "unit": "bond updates/s", "cores": cores, "kind": "oracle",
-            "sample": "oracle (NumPy FP64, LAPACK SVD): second Trotter step of %dx%d at chi=%d, bonds saturated "
-                      "(%d bond updates + observables in %.1f s; same grid, reduced chi)"
-                      % (Lx, Ly, sample_chi, n_upd, dt)}
+    return {"value": n / secs, "unit": "bond updates/s", "cores": cores, "kind": "oracle",
+            "sample": smp.describe(n, secs)}
 
 
 def run_reference(args, Lx, Ly):
+    """The oracle as the reference arm: each step is one bond update at the identical shape
+    (OracleSample); W untimed steps, then K timed ones."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    steps = []
-    for _ in range(args.warmup + args.steps):
-        steps.append(cpu_baseline(Lx, Ly, args.cpu_sample_chi, TEMP_DTHETA))
-    timed = steps[args.warmup:]
-    value = statistics.mean(s["value"] for s in timed)
+    smp = OracleSample(Lx, Ly, args.chi)
+    phi = J * DT
+    for _ in range(args.warmup):
+        smp.update(phi)
+    n = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        k, t = smp.update(phi)
+        n += k
+        secs += t
+    value = n / secs
+    cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": "bond updates/s at %dx%d chi=%d" % (Lx, Ly, args.chi), "value": value,
             "unit": "bond updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "TFIM %dx%d grouped MPS, chi=%d (reference sampled at chi=%d), mid temperature, "
-                                   "J=-1 h=2 dt=0.25, 2nd-order Trotter" % (Lx, Ly, args.chi, args.cpu_sample_chi)},
-            "cpu_baseline": timed[-1],
+            "config": {"workload": "TFIM %dx%d grouped MPS, bond updates at chi=%d (every bond at chi), one "
+                                   "adjacent gate per step; J=-1 h=2 dt=0.25" % (Lx, Ly, args.chi)},
+            "cpu_baseline": {"value": value, "unit": "bond updates/s", "cores": cores, "kind": "oracle",
+                             "sample": smp.describe(n, secs)},
             "e2e": {"value": value, "unit": "bond updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fp64_form_rate(lib, m_split, Lx, Ly, n_updates, stream):
+    """The FP64 form (complex128, exact SVD truncation) on the evolved state of the timed run:
+    the split-form MPS is written to a checkpoint, converted to complex128 and loaded as an FP64
+    handle, which then applies adjacent gates between the middle blocks; device time by CUDA
+    events on its stream."""
+    import torch
+
+    gates = middle_adjacent_gates(lib.schedule_gates(Lx, Ly), Lx)
+    with tempfile.TemporaryDirectory() as td:
+        a = os.path.join(td, "split.bin")
+        b = os.path.join(td, "fp64.bin")
+        m_split.save(a)
+        lib.convert_checkpoint(a, b, "fp64")
+        g = lib.MPS.load_checkpoint(b, stream=stream.cuda_stream)
+    phi = J * DT
+    g.apply_gates(gates[0], 1, phi)  # brings the centre next to the middle blocks (untimed)
+    torch.cuda.synchronize()
+    st0 = g.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n_updates):
+        g.apply_gates(gates[(i + 1) % len(gates)], 1, phi)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = g.stats()["truncations"] - st0["truncations"]
+    g.close()
+    return {"value": n / (ms / 1e3), "unit": "bond updates/s", "bond_updates": n, "ms": ms,
+            "sample": "FP64 form (complex128 storage, FP64 GEMMs, exact truncation by one-sided Jacobi SVD) on the "
+                      "evolved %dx%d state at chi=%d: %d adjacent gate(s) between the middle blocks" %
+                      (Lx, Ly, m_split.cfg.chi_max, n)}
 
 
 def reduce_over_ranks(ms, updates, dist, device):
@@ -239,6 +363,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     st0 = m.stats()
+    cnt0 = m.counters()
     l0 = lib.launch_count()
     if dist:
         dist.barrier()
@@ -254,6 +379,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = lib.launch_count() - l0
     st1 = m.stats()
+    cnt1 = m.counters()
     clk = clocks.stop()
     # one more step with per-launch-site CUDA-event timing (kept out of the timed region)
     lib.kernel_timing(True)
@@ -295,23 +421,27 @@ def main():
     peaks = read_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6792.1)
     tc_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1715.0))
-    fp32_peak = 69.9   # measured FP32 CUDA-core matmul rate of this GPU (bench.py --peaks)
-    fp64_peak = 1.10   # measured FP64 matmul rate of this GPU (bench.py --peaks)
+    # FP32 CUDA-core peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
+    # (the measured FP32 matmul rate, bench.py --peaks, is 69.9); FP64: the measured matmul rate
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fp64_peak = 1.10
 
     def roofline(name, kms, kn, kwork):
         if kms <= 0:
             return None
-        if "in-block gate" in name or "Householder" in name:  # bytes
+        if "in-block gate" in name:  # bytes
             r = {"bound": "hbm", "achieved": kwork / (kms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
         elif "tcgen05" in name:  # useful complex flops; the tensor pipe executes 3 bf16 products each
             r = {"bound": "tensor", "achieved": 3 * kwork / (kms / 1e3) / 1e12, "peak": tc_peak, "unit": "TFLOP/s",
                  "useful_tflops": kwork / (kms / 1e3) / 1e12,
                  "peak_source": "measured (MEASURED_PEAKS.json bf16 sustained)"}
-        else:  # CUDA-core arithmetic
-            pk = fp64_peak if args.prec == "fp64" else fp32_peak
+        else:  # CUDA-core arithmetic (the Householder reduction counted as 16 n^3 / 3 flops per launch)
+            fp64 = args.prec == "fp64"
+            pk = fp64_peak if fp64 else fp32_peak
             r = {"bound": "alu", "achieved": kwork / (kms / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
-                 "peak_source": "measured (torch matmul, bench.py --peaks)"}
+                 "peak_source": "measured FP64 matmul rate" if fp64 else
+                 "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
         r["kernel"] = name
@@ -342,11 +472,19 @@ def main():
             "roofline_tensorcore_gemm": roof_tc,
             "e2e": {"value": e2e_updates / e2e_s, "unit": "bond updates/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "kernel_sites_ms": {k: round(v[0], 3) for k, v in ktimes.items()}}
+            "kernel_sites_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
+            "kernel_sites_tflops": {k: round(v[2] / (v[0] / 1e3) / 1e12, 3) for k, v in ktimes.items()
+                                    if v[0] > 0 and v[2] > 0 and "in-block" not in k},
+            "counters_per_step": {k: (cnt1[k] - cnt0[k]) / args.steps for k in cnt1}}
+    if args.fp64_updates > 0 and world == 1:
+        line["fp64_form"] = fp64_form_rate(lib, m, Lx, Ly, args.fp64_updates, stream)
+    m.close()
     if args.serve_jobs > 0 and world == 1:
-        line["serve"] = serve_run(args.serve_jobs, args.prec)
+        line["serve"] = serve_run(args.serve_jobs, args.serve_steps, args.prec)
+    if args.batch_mps > 0 and world == 1:
+        line["batched"] = batched_run(lib, args.batch_mps, args.prec)
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
-        line["cpu_baseline"] = cpu_baseline(Lx, Ly, args.cpu_sample_chi, TEMP_DTHETA)
+        line["cpu_baseline"] = cpu_baseline(Lx, Ly, args.chi, args.cpu_updates)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

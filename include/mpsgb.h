@@ -49,17 +49,24 @@ typedef enum {
 } mpsgb_status;
 
 /* Arithmetic of the path.
- *   FP64         complex128 storage, every contraction and the truncation core in FP64.
- *   SPLIT_TF32X3 reserved (TF32 splits; not available in this build).
+ *   FP64         complex128 storage, every contraction in FP64; every spanned bond is truncated by
+ *                the SVD of the centre block (one-sided Jacobi, no Gram matrix), which resolves
+ *                Schmidt values down to the rounding floor.  The accuracy reference.
+ *   SPLIT_TF32X3 reserved (TF32 splits; not available in this build: EINVAL).
  *   SPLIT_BF16X3 complex64 storage; the block-sized contractions (Grams, left factors, new blocks,
  *                transfer and environment products) on the tcgen05 tensor cores: every FP32
  *                component is split into two BF16 terms (hi + lo, 16 significant bits) and a
  *                real product is hi*hi + hi*lo + lo*hi with FP32 accumulation; the truncation core
- *                (bond x bond products, eigensolves) in FP32 on CUDA cores; weights and F in FP64.
+ *                in FP32 on CUDA cores: the left Gram factorised by Cholesky (its eigenvectors when
+ *                it is numerically singular), one Hermitian eigensolve of the 2 chi x 2 chi core;
+ *                weights and F in FP64.
  *   FP32         complex64 storage, all contractions on FP32 CUDA cores (reference form for
  *                the split forms). */
 typedef enum { MPSGB_FP64 = 0, MPSGB_SPLIT_TF32X3 = 1, MPSGB_SPLIT_BF16X3 = 2, MPSGB_FP32 = 3 } mpsgb_precision;
-/* Non-adjacent gates: MPO route (Sec. III) or SWAP routing. */
+/* Non-adjacent gates: MPO route (Sec. III: the rank-2 MPO spans the bonds between the two blocks,
+ * each truncated in turn) or SWAP routing (block q is moved next to block p by two-site SWAP updates,
+ * the gate is one two-site update, and the block is moved back; every two-site update is an SVD
+ * truncation).  SWAP routing needs chi * d <= 4096 (EINVAL at creation otherwise). */
 typedef enum { MPSGB_ROUTE_MPO = 0, MPSGB_ROUTE_SWAP = 1 } mpsgb_route;
 typedef enum { MPSGB_LAYER_X = 0, MPSGB_LAYER_ZZ = 1 } mpsgb_layer;
 typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2 } mpsgb_obs;
@@ -109,7 +116,9 @@ int mpsgb_apply_gates(mpsgb_handle h, int first, int count, double phi);
 int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order, int nsteps);
 
 /* Re-compress the whole MPS to bond dimension chi <= chi_max by a left-to-right sequential SVD
- * sweep; multiplies F_MPS by every truncation fidelity.  Errors: EINVAL for chi < 1 or > chi_max. */
+ * sweep: the truncation of Sec. III (keep the chi largest singular values of each bond with the
+ * orthogonality centre on it, renormalise) applied bond by bond without a gate; multiplies F_MPS
+ * by every truncation fidelity.  Errors: EINVAL for chi < 1 or > chi_max. */
 int mpsgb_truncate(mpsgb_handle h, int chi);
 
 /* Expectation value (Eq. Z_tot, Eq. z2_tot, or <X_tot> = (1/n) sum_j <X_j>) of the current,
@@ -124,23 +133,33 @@ int mpsgb_observables(mpsgb_handle h, double out[4]);
 int mpsgb_fidelity(mpsgb_handle h, double* F);
 
 /* Schmidt values across bond `bond` (0 .. nblocks-2, between blocks bond and bond+1), descending,
- * written to out[0 .. min(cap, n)-1]; *n receives the bond dimension.  Moves the orthogonality
- * centre (the state is unchanged).  Errors: EINVAL for a bad bond or null pointer. */
+ * written to out[0 .. min(cap, n)-1]; *n receives the bond dimension.  These are the singular
+ * values of Sec. III whose discarded squares make up 1 - F at a truncation.  Moves the
+ * orthogonality centre (the state is unchanged).  Errors: EINVAL for a bad bond or null pointer. */
 int mpsgb_singular_values(mpsgb_handle h, int bond, double* out, int cap, int* n);
 
 /* Current bond dimensions (nblocks-1 values) to out[0 .. cap-1]; *n receives nblocks-1. */
 int mpsgb_bond_dims(mpsgb_handle h, int* out, int cap, int* n);
 
 /* Device memory a handle of this config holds for its blocks, chi^2 * dmax * nblocks * element
- * size (the admission figure of the serving loop), to the host *bytes.  Host only. */
+ * size, to the host *bytes.  Not from the paper: the admission figure of the serving loop (the
+ * paper keeps its MPS sites in host RAM and moves them to the GPU as needed).  Host only. */
 int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes);
 
-/* Advance `count` independent handles by nsteps Trotter steps each with the J, h, dt and order of
- * their configs; handles are advanced concurrently (one host thread per handle, each on its own
- * stream).  flags: reserved, pass 0.  Returns the first failing status. */
-int mpsgb_batch_step(mpsgb_handle* hs, int count, int nsteps, int flags);
+/* Batched advance of many independent MPS (the task's batched workload; the paper evolves one MPS
+ * at a time): every handle in hs[0 .. count-1] applies nlayers Trotter layers U(dt) (Eq.
+ * trotter_step for order 2, X then ZZ for order 1) with the J, h, dt and order of its own config.
+ * Handles advance concurrently, one host thread and the handle's own CUDA stream each, so their
+ * kernels overlap on the device.  use_graph must be 0: the truncation decisions (kept counts,
+ * fidelities) are read back to the host after every eigensolve or SVD, so a layer is not a
+ * fixed launch sequence that a CUDA graph could replay; EINVAL otherwise.  The handles must be
+ * distinct.  Returns the first failing status (with the handle's index in the message). */
+int mpsgb_batch_step(mpsgb_handle* hs, int count, int nlayers, int use_graph);
 
-/* Write / read a checkpoint: config, bond dims, centre, F_MPS, counters and all blocks.
+/* Write / read a checkpoint: config, bond dims, centre, F_MPS, counters and all blocks.  Not from
+ * the paper: persistence of this library (file layout: "MPSGBv1\0", the config struct, four ints
+ * {element bytes, blocks, centre, 0}, F as a double, five 64-bit counters, the bond dims as ints,
+ * then every block (left, d, right) row-major complex in the form's element type).
  * mpsgb_load creates a new handle (alloc and stream as in mpsgb_create).  Errors: EINVAL for an
  * unreadable or mismatched file, ENOMEM, EDEVICE. */
 int mpsgb_save(mpsgb_handle h, const char* path);
@@ -164,12 +183,18 @@ int mpsgb_stats(mpsgb_handle h, long long out[5]);
  * Not from the paper: a robustness control of this library. */
 long long mpsgb_set_wait_limit(long long cycles);
 
+/* All counters of a handle, in this order: bond truncations, inter-block gates, centre moves,
+ * eigensolver or SVD calls, their sweeps, Gram matrices factorised by Cholesky (complex64 forms),
+ * Gram matrices too close to singular for Cholesky (the eigenvector factor was taken).  Up to cap
+ * values to out; *n receives the number of counters (7).  Not from the paper: diagnostics. */
+int mpsgb_counters(mpsgb_handle h, long long* out, int cap, int* n);
+
 /* Number of CUDA kernels the library has launched in this process (all handles). */
 unsigned long long mpsgb_launch_count(void);
 
 /* Device-time measurement of the library's launch sites with CUDA events on their own streams.
  * mpsgb_kernel_timing(1) resets the totals and starts recording (0 stops); mpsgb_kernel_times
- * synchronises on the recorded events and returns, for launch site `site` (0 .. 8, see
+ * synchronises on the recorded events and returns, for launch site `site` (0 .. 10, see
  * mpsgb_kernel_site_name), the summed device time in ms, the launch count and the useful work of
  * those launches (real flops for arithmetic sites -- 16 n^3 / 3 for the Householder reduction of an
  * n x n Hermitian matrix; bytes moved for the in-block gate; 0 for the Jacobi SVD, whose work

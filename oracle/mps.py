@@ -162,6 +162,61 @@ class MPS:
             self.blocks[m + 1] = np.tensordot(sk[:, None] * Vh[:k], self.blocks[m + 1], axes=([1], [0]))
         self.centre = q
 
+    # ---------------------------------------------------------------- SWAP routing
+    def _two_site(self, m, swap=False, phase=None, centre_left=True):
+        """Two-site update of blocks m, m+1 (the centre on one of them): theta = A B as a dense
+        (left, d_m, d_m+1, right) tensor, optionally with a diagonal two-qubit phase on the two
+        physical indices or with the two physical legs exchanged (a SWAP of the blocks), then the
+        SVD of theta as a (left * d) x (d' * right) matrix with numpy.linalg.svd, truncated like
+        the MPO sweep (min(chi, numerical rank) values, f = kept / total, renormalised).  The
+        kept singular values go into block m (centre_left) or block m+1."""
+        A, B = self.blocks[m], self.blocks[m + 1]
+        l, da, _ = A.shape
+        _, db, r = B.shape
+        th = np.tensordot(A, B, axes=([2], [0]))  # (l, da, db, r)
+        if phase is not None:
+            th = th * phase[None, :, :, None]
+        if swap:
+            th = th.transpose(0, 2, 1, 3)
+            da, db = db, da
+        M = th.reshape(l * da, db * r)
+        U, s, Vh = np.linalg.svd(M, full_matrices=False)
+        k = _rank_keep(s, M.shape, self.chi)
+        tot = float(np.sum(s * s))
+        kept = float(np.sum(s[:k] ** 2))
+        f = kept / tot
+        if k < len(s) and s[k] > 0:
+            self.cut_gaps.append((s[k - 1] - s[k]) / s[0])
+        self.F *= f
+        self.fidelities.append(f)
+        self.kept_norms.append(kept)
+        sk = s[:k] / np.sqrt(kept)
+        if centre_left:
+            self.blocks[m] = (U[:, :k] * sk[None, :]).reshape(l, da, k)
+            self.blocks[m + 1] = Vh[:k].reshape(k, db, r)
+        else:
+            self.blocks[m] = U[:, :k].reshape(l, da, k)
+            self.blocks[m + 1] = (sk[:, None] * Vh[:k]).reshape(k, db, r)
+        if swap:
+            self.layout[m], self.layout[m + 1] = self.layout[m + 1], self.layout[m]
+
+    def zz_inter_swap(self, gate, phi):
+        """One inter-block exp(-i phi Z_i Z_j) by SWAP routing: block q is swapped leftwards next
+        to block p (q - p - 1 two-site SWAP updates, centre travelling left), the gate is applied
+        as a diagonal phase in one two-site update of blocks p and p+1, and the block is swapped
+        back (centre travelling right).  Every two-site update is an SVD truncation, so a gate of
+        block distance k costs 2 (k - 1) + 1 of them.  Ends with the centre on block q."""
+        p, q, _, _, ti, tj = gate
+        self.move_centre(q)
+        for m in range(q - 1, p, -1):
+            self._two_site(m, swap=True, centre_left=True)
+        zi = self._zdiag(len(self.layout[p]["qubits"]), ti)
+        zj = self._zdiag(len(self.layout[p + 1]["qubits"]), tj)
+        self._two_site(p, phase=np.exp(-1j * phi * np.outer(zi, zj)), centre_left=False)
+        for m in range(p + 1, q):
+            self._two_site(m, swap=True, centre_left=False)
+        self.centre = q
+
     # ---------------------------------------------------------------- observables
     def bond_dims(self):
         return [b.shape[2] for b in self.blocks[:-1]]
@@ -276,8 +331,9 @@ def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0):
     return m
 
 
-def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False):
-    """TEBD run of Eq. trotter_step (order 2) or X-then-ZZ (order 1).
+def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False, route="mpo"):
+    """TEBD run of Eq. trotter_step (order 2) or X-then-ZZ (order 1); inter-block gates by the MPO
+    sweep (route "mpo", Sec. III) or by SWAP routing (route "swap").
 
     Returns a dict with per-step arrays (entry 0 = initial state): Z, Z2, X, F, plus the
     list of truncation fidelities, final bond dims and the MPS itself.
@@ -304,7 +360,10 @@ def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False):
         psi.x_layer(alpha)
         psi.zz_intra(phi, intra)
         for g in inter:
-            psi.zz_inter(g, phi)
+            if route == "swap":
+                psi.zz_inter_swap(g, phi)
+            else:
+                psi.zz_inter(g, phi)
         if order == 2:
             psi.x_layer(alpha)
         record()

@@ -45,7 +45,6 @@ int check_config(const mpsgb_config* c) {
   if (!c) return fail(MPSGB_EINVAL, "null config");
   if (c->prec < MPSGB_FP64 || c->prec > MPSGB_FP32) return fail(MPSGB_EINVAL, "unknown precision");
   if (c->route != MPSGB_ROUTE_MPO && c->route != MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "unknown route");
-  if (c->route == MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "SWAP routing is not available in this build");
   if (c->prec == MPSGB_SPLIT_TF32X3) return fail(MPSGB_EINVAL, "SPLIT_TF32X3 is not available in this build");
   if (!std::isfinite(c->theta)) return fail(MPSGB_EINVAL, "theta is not finite");
   if (c->chi_max < 1 || c->chi_max > 8192) return fail(MPSGB_EINVAL, "chi_max must be in 1..8192");
@@ -161,11 +160,16 @@ int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes) {
   return MPSGB_OK;
 }
 
-int mpsgb_batch_step(mpsgb_handle* hs, int count, int nsteps, int flags) {
-  (void)flags;
-  if (!hs || count < 0 || nsteps < 0) return fail(MPSGB_EINVAL, "bad batch arguments");
-  for (int i = 0; i < count; ++i)
+int mpsgb_batch_step(mpsgb_handle* hs, int count, int nlayers, int use_graph) {
+  if (!hs || count < 0 || nlayers < 0) return fail(MPSGB_EINVAL, "bad batch arguments");
+  if (use_graph != 0)
+    return fail(MPSGB_EINVAL, "use_graph: truncation decisions are read back on the host, no CUDA graph replay");
+  const int nsteps = nlayers;
+  for (int i = 0; i < count; ++i) {
     if (!hs[i] || !hs[i]->e) return fail(MPSGB_EINVAL, "null handle in batch");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(MPSGB_EINVAL, "the same handle twice in a batch");
+  }
   std::vector<int> st(count, 0);
   std::vector<std::string> msg(count);
   std::vector<std::thread> th;
@@ -236,6 +240,15 @@ long long mpsgb_set_wait_limit(long long cycles) {
   long long prev = mpsgb::wait_limit_cycles();
   mpsgb::set_wait_limit_cycles(cycles > 0 ? cycles : 4000000000LL);
   return prev;
+}
+
+int mpsgb_counters(mpsgb_handle h, long long* out, int cap, int* n) {
+  if (!h || !h->e || !n || (cap > 0 && !out)) return fail(MPSGB_EINVAL, "null argument");
+  const auto& s = h->e->stats;
+  const long long v[7] = {s.truncations, s.gates, s.centre_moves, s.eig_calls, s.eig_sweeps, s.chol_ok, s.chol_fallbacks};
+  *n = 7;
+  for (int i = 0; i < cap && i < 7; ++i) out[i] = v[i];
+  return MPSGB_OK;
 }
 
 unsigned long long mpsgb_launch_count(void) { return __atomic_load_n(&mpsgb::g_launch_count, __ATOMIC_RELAXED); }

@@ -68,7 +68,15 @@ void set_wait_limit_cycles(long long cycles);
 // kt_begin / kt_end bracket the launches of one site on their stream and the
 // accumulated device time is read back by mpsgb_kernel_times().
 enum KtSite { KT_GEMM = 0, KT_EIG_PAIR, KT_EIG_UPDATE, KT_EIG_SMALL, KT_PHYS, KT_TC_GEMM, KT_HETRD, KT_TRIVEC,
-              KT_SVD, KT_NSITES };
+              KT_SVD, KT_GEMM_EIG, KT_GEMM_CHOL, KT_NSITES };
+// timing site that CUDA-core GEMMs issued on this thread are charged to (KT_GEMM unless a caller
+// sets another for its scope with GemmSite)
+extern thread_local int g_gemm_site;
+struct GemmSite {
+  int prev;
+  explicit GemmSite(int site) : prev(g_gemm_site) { g_gemm_site = site; }
+  ~GemmSite() { g_gemm_site = prev; }
+};
 extern bool g_kt_enabled;
 void kt_begin_impl(int site, cudaStream_t st);
 void kt_end_impl(int site, cudaStream_t st);

@@ -410,6 +410,7 @@ size_t eigh_workspace_bytes(int n, int batch, int real_bytes) {
 template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
          long long ldv, long long sV, int batch, void* workspace, int nvec) {
+  GemmSite site(KT_GEMM_EIG);
   if (n <= 0 || batch <= 0) return 0;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   auto take = [&](size_t bytes) { unsigned char* p = ws; ws += (bytes + 255) & ~size_t(255); return p; };

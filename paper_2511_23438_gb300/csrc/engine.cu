@@ -154,6 +154,9 @@ class EngineT : public Engine {
   size_t tcws_bytes = 0;
   int* derr = nullptr;    // device error word of bounded waits in kernels
   bool exact = false;     // FP64 form: truncation and centre moves by the SVD (one-sided Jacobi)
+  long long stats_chol_fallbacks = 0;
+  std::vector<int> kpos;  // qubits of the block at each position (L.k except inside a SWAP-routed gate)
+  bool swap_route = false;  // truncation cores whose G was too close to singular for Cholesky
 
   // Block-sized contraction: tensor cores in the split form (when every dimension is at least
   // 64), FP32 / FP64 CUDA cores otherwise.
@@ -190,7 +193,8 @@ class EngineT : public Engine {
     if (e != cudaSuccess) throw Fail{MPSGB_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e)};
     check(what);
   }
-  int d(int b) const { return 1 << L.k[b]; }
+  // local dimension of the block at position b (SWAP routing exchanges blocks transiently)
+  int d(int b) const { return 1 << kpos[b]; }
   int left(int b) const { return b == 0 ? 1 : dims[b - 1]; }
   int right(int b) const { return b == L.N - 1 ? 1 : dims[b]; }
   int cap_bond(int m) const { return (int)std::min<double>(cfg.chi_max, L.bound[m]); }
@@ -203,6 +207,8 @@ class EngineT : public Engine {
     std::string err;
     if (!make_layout(c.Lx, c.Ly, L, err)) throw Fail{MPSGB_EINVAL, err};
     if (c.chi_max < 1) throw Fail{MPSGB_EINVAL, "chi_max must be >= 1"};
+    kpos = L.k;
+    swap_route = c.route == MPSGB_ROUTE_SWAP;
     double mb = 1;
     for (double b : L.bound) mb = std::max(mb, b);
     chi_eff = (int)std::min<double>(c.chi_max, mb);
@@ -223,10 +229,19 @@ class EngineT : public Engine {
     size_t obs = sizeof(C) * (4 * cap + 16 * c2);
     size_t eigws = eigh_workspace_bytes((int)n2, 1, (int)sizeof(R));
     ar.size = std::max(phase, obs) + eigws + (64 << 10);
+    if (swap_route) {
+      // two-site tensors of SWAP routing: theta and its permuted copy, Vh, U ((chi d)^2 each) and the
+      // SVD's working copy; bounded so that a two-site SVD stays a small problem
+      const long long w = (long long)chi_eff * dmax;
+      if (w > 4096) throw Fail{MPSGB_EINVAL, "SWAP routing needs chi * d <= 4096 (two-site SVD of a (chi d)^2 matrix)"};
+      const size_t sw = sizeof(C) * 4 * (size_t)w * w + sizeof(double) * 2 * w +
+                        svd_rows_workspace_bytes((int)w, (int)w, 1, (int)sizeof(R)) + (1 << 20);
+      ar.size = std::max(ar.size, sw);
+    }
     if (exact) {
       // A^H copy, Vh, U, T (<= 4 cap and (2 chi)^2 each) and the SVD's own working copy
       const size_t svdws = svd_rows_workspace_bytes((int)n2, (int)(4 * cap / n2 + 1), 1, (int)sizeof(R));
-      ar.size = sizeof(C) * (8 * cap + 3 * n2 * n2) + sizeof(double) * 4 * n2 + svdws + (1 << 20);
+      ar.size = std::max<size_t>(ar.size, sizeof(C) * (8 * cap + 3 * n2 * n2) + sizeof(double) * 4 * n2 + svdws + (1 << 20));
       ar.size = std::max(ar.size, obs + (size_t)(64 << 10));
     }
     ar.base = (char*)mem.get(ar.size);
@@ -350,18 +365,12 @@ class EngineT : public Engine {
     if (first < 0 || count < 0 || first + count > (int)L.inter.size())
       throw Fail{MPSGB_EINVAL, "gate range outside the schedule"};
     last_f_min = 1.0;
-    for (int i = first; i < first + count; ++i) {
-      if (exact) gate_exact(L.inter[i], phi);
-      else gate(L.inter[i], phi);
-    }
+    for (int i = first; i < first + count; ++i) any_gate(L.inter[i], phi);
     return MPSGB_OK;
   }
   void inter_layer(double phi) {
     last_f_min = 1.0;
-    for (auto& g : L.inter) {
-      if (exact) gate_exact(g, phi);
-      else gate(g, phi);
-    }
+    for (auto& g : L.inter) any_gate(g, phi);
   }
   int step(double J, double hx, double dt, int order, int nsteps) override {
     double alpha = order == 2 ? 0.5 * hx * dt : hx * dt, phi = J * dt;
@@ -375,10 +384,12 @@ class EngineT : public Engine {
 
 
   // ---------------------------------------------------------- exact route (FP64 form)
-  // numerical rank of a descending spectrum of a rows x cols matrix: s > s_0 max(rows, cols) eps
+  // numerical rank of a descending spectrum of a rows x cols matrix: s > s_0 max(rows, cols) eps,
+  // eps of the working precision (values below it are rounding noise of the stored blocks)
   static int rank_of(const std::vector<double>& s, long long rows, long long cols, int cap_) {
     if (s.empty() || !(s[0] > 0)) return 0;
-    const double tol = s[0] * (double)std::max(rows, cols) * 2.220446049250313e-16;
+    const double eps = sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920929e-7;
+    const double tol = s[0] * (double)std::max(rows, cols) * eps;
     int c = 0;
     while (c < (int)s.size() && c < cap_ && s[c] > tol) ++c;
     return c;
@@ -398,6 +409,7 @@ class EngineT : public Engine {
     stats.eig_calls++;
     if (sw == -1) throw Fail{MPSGB_ETIMEDOUT, "Jacobi SVD did not converge within its sweep limit"};
     if (sw == -2) throw Fail{MPSGB_ETIMEDOUT, "Jacobi SVD: a bounded grid barrier timed out"};
+    if (sw == -5) throw Fail{MPSGB_ESTATE, "Jacobi SVD: the matrix is not finite"};
     if (sw < 0) throw Fail{MPSGB_EDEVICE, "Jacobi SVD: launch or device error"};
     stats.eig_sweeps += sw;
   }
@@ -487,6 +499,77 @@ class EngineT : public Engine {
     check("gate");
   }
 
+
+  // ---------------------------------------------------------- SWAP routing
+  // Two-site update of blocks m, m+1 (the centre on one of them): theta = A B as a (l d_m) x (d_m+1 r)
+  // matrix, with a diagonal two-qubit phase exp(-i phi z_a z_b) on the physical indices (bit shift_a
+  // of block m, shift_b of block m+1) or with the physical legs exchanged (the blocks swap places),
+  // then its SVD truncated to min(chi, numerical rank) values, f = kept / total, renormalised; the
+  // singular values go into block m (centre_left) or block m+1.
+  void two_site(int m, bool swap, bool with_phase, double phi, int shift_a, int shift_b, bool centre_left) {
+    ar.off = 0;
+    const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+    const int l = left(m), da = d(m), mid = dims[m], db = d(m + 1), r = right(m + 1);
+    const long long rowsA = (long long)l * da, colsB = (long long)db * r;
+    C* Th = ar.take<C>((size_t)(rowsA * colsB));
+    if (!Th) throw Fail{MPSGB_ENOMEM, "workspace exhausted in a two-site update"};
+    mm((int)rowsA, (int)colsB, mid, one, rowmajor<R>(blk[m], mid), rowmajor<R>(blk[m + 1], colsB), zero,
+       rowmajor<R>(Th, colsB));
+    if (with_phase) two_site_phase<R>(stream, l, da, db, r, Th, phi, shift_a, shift_b);
+    C* X = Th;
+    int prow = (int)rowsA, pcol = (int)colsB;
+    if (swap) {
+      prow = l * db;
+      pcol = da * r;
+      X = ar.take<C>((size_t)prow * pcol);
+      if (!X) throw Fail{MPSGB_ENOMEM, "workspace exhausted in a two-site update"};
+      // X[(a, t), (s, b)] = theta[a, s, t, b]
+      View<R> src;
+      src.ptr = Th;
+      src.row = split(db, r, (long long)da * db * r);
+      src.col = split(r, 1, (long long)db * r);
+      src.conj = false;
+      copy_view<R, R>(stream, prow, pcol, src, rowmajor<R>(X, pcol));
+    }
+    C *Vh, *U;
+    double* ds;
+    std::vector<double> s;
+    jsvd(X, prow, pcol, Vh, U, ds, s);
+    const int k = std::max(1, rank_of(s, prow, pcol, std::min(cfg.chi_max, chi_eff)));
+    double kept = 0, total = 0;
+    for (int i = 0; i < (int)s.size(); ++i) { total += s[i] * s[i]; if (i < k) kept += s[i] * s[i]; }
+    if (!(kept > 0)) throw Fail{MPSGB_ESTATE, "zero state at a truncation"};
+    const double f = kept / total;
+    F *= f;
+    last_f_min = std::min(last_f_min, f);
+    stats.truncations++;
+    const double rs = 1.0 / std::sqrt(kept);
+    copy_view<R, R>(stream, prow, k, rowmajor<R>(U, prow), rowmajor<R>(spare, k));
+    if (centre_left) scale_cols<R>(stream, prow, k, spare, k, ds, rs);
+    std::swap(blk[m], spare);
+    copy_view<R, R>(stream, k, pcol, rowmajor<R>(Vh, pcol), rowmajor<R>(spare, pcol));
+    if (!centre_left) scale_rows<R>(stream, k, pcol, spare, pcol, ds, rs);
+    std::swap(blk[m + 1], spare);
+    dims[m] = k;
+    if (swap) std::swap(kpos[m], kpos[m + 1]);
+    check("two-site update");
+  }
+  // inter-block gate by SWAP routing: block q travels left next to block p through two-site SWAP
+  // updates, the gate is one two-site update with a diagonal phase, and the block travels back
+  void gate_swap(const Layout::Gate& g, double phi) {
+    const int p = g.p, q = g.q;
+    move_centre(q);
+    for (int m = q - 1; m > p; --m) two_site(m, true, false, 0.0, 0, 0, true);
+    two_site(p, false, true, phi, kpos[p] - 1 - g.ti, kpos[p + 1] - 1 - g.tj, false);
+    for (int m = p + 1; m < q; ++m) two_site(m, true, false, 0.0, 0, 0, false);
+    centre = q;
+    stats.gates++;
+  }
+  void any_gate(const Layout::Gate& g, double phi) {
+    if (swap_route) gate_swap(g, phi);
+    else if (exact) gate_exact(g, phi);
+    else gate(g, phi);
+  }
   // ---------------------------------------------------------- centre moves (QR / LQ through the Gram)
   void move_right(int m) {  // block m becomes left-isometric, centre to m+1
     ar.off = 0;
@@ -498,6 +581,20 @@ class EngineT : public Engine {
     void* ws = ar.take<char>(eigh_workspace_bytes(r, 1, sizeof(R)));
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
     mm(r, r, l * dd, one, transposed<R>(blk[m], r, true), rowmajor<R>(blk[m], r), zero, rowmajor<R>(G, r));
+    if (l * dd >= r) {  // QR through the Cholesky factor of the Gram: Q = M C^{-H}, R = C^H
+      C* Ci = nullptr;
+      if (C* Cf = try_chol(r, G, Ci)) {
+        mm(l * dd, r, r, one, rowmajor<R>(blk[m], r), transposed<R>(Ci, r, true), zero, rowmajor<R>(spare, r));
+        std::swap(blk[m], spare);
+        const int dn = d(m + 1), rn = right(m + 1);
+        mm(r, dn * rn, r, one, transposed<R>(Cf, r, true), rowmajor<R>(blk[m + 1], (long long)dn * rn), zero,
+           rowmajor<R>(spare, (long long)dn * rn));
+        std::swap(blk[m + 1], spare);
+        stats.centre_moves++;
+        check("move right");
+        return;
+      }
+    }
     std::vector<double> hw;
     eig(r, G, w, U, ws, hw);
     int rp = std::max(1, count_above(hw, tau, std::min(r, l * dd)));
@@ -528,6 +625,19 @@ class EngineT : public Engine {
     void* ws = ar.take<char>(eigh_workspace_bytes(l, 1, sizeof(R)));
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
     mm(l, l, (int)row, one, rowmajor<R>(blk[m], row), transposed<R>(blk[m], row, true), zero, rowmajor<R>(G, l));
+    if (row >= l) {  // LQ through the Cholesky factor of the Gram: B = C Q, Q = C^{-1} B
+      C* Ci = nullptr;
+      if (C* Cf = try_chol(l, G, Ci)) {
+        mm(l, (int)row, l, one, rowmajor<R>(Ci, l), rowmajor<R>(blk[m], row), zero, rowmajor<R>(spare, row));
+        std::swap(blk[m], spare);
+        const int lq = left(m - 1), dq = d(m - 1);
+        mm(lq * dq, l, l, one, rowmajor<R>(blk[m - 1], l), rowmajor<R>(Cf, l), zero, rowmajor<R>(spare, l));
+        std::swap(blk[m - 1], spare);
+        stats.centre_moves++;
+        check("move left");
+        return;
+      }
+    }
     std::vector<double> hw;
     eig(l, G, w, U, ws, hw);
     int lp = std::max(1, count_above(hw, tau, std::min<long long>(l, row)));
@@ -565,8 +675,10 @@ class EngineT : public Engine {
   // ---------------------------------------------------------- truncation core
   // G: 2r x 2r left Gram, E: 2r x 2r right environment (both overwritten / read).
   // Outputs: k, WL (r2 x k), Kc (k x r2, scaled by 1/sqrt(kept)), kept, total.
-  void core(int r2, int rows, int kcap, C* G, C* E, C* WL, C* Kc, int& k, double& kept, double& total) {
+  void core(int r2, int rows, int kcap, C* G, C* E, C* WL, C* Kc, int& k, double& kept, double& total,
+            bool may_be_full_rank = true) {
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+    if (may_be_full_rank && rows >= r2 && core_chol(r2, kcap, G, E, WL, Kc, k, kept, total)) return;
     C* U = ar.take<C>((size_t)r2 * r2);
     R* Dv = ar.take<R>(r2);
     C* Gs = ar.take<C>((size_t)r2 * r2);
@@ -601,6 +713,71 @@ class EngineT : public Engine {
     View<R> vkh; vkh.ptr = V; vkh.row = plain(1); vkh.col = plain(rG); vkh.conj = true;
     gemm<R>(stream, k, r2, rG, cmake<R>((R)(1.0 / std::sqrt(kept)), 0), vkh, transposed<R>(Gs, rG, true), zero,
             rowmajor<R>(Kc, r2));
+  }
+
+  // Cholesky factor of the n x n Gram G (copied, G untouched) and its inverse, from the arena: Cf
+  // (lower) and Ci = Cf^{-1} (lower); nullptr if G is numerically singular (a pivot at or below
+  // 32 eps G_jj), in which case the arena is left as it was.
+  C* try_chol(int n, const C* G, C*& Ci) {
+    const size_t save = ar.off;
+    C* Cf = ar.take<C>((size_t)n * n);
+    Ci = ar.take<C>((size_t)n * n);
+    const size_t mark = ar.off;
+    void* cws = ar.take<char>(chol_workspace_bytes(n, sizeof(R)));
+    int* flag = ar.take<int>(4);
+    if (!flag) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the Cholesky factorisation"};
+    cudaMemcpyAsync(Cf, G, sizeof(C) * (size_t)n * n, cudaMemcpyDeviceToDevice, stream);
+    const double rel = 32.0 * (sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920929e-7);
+    if (chol_inv<R>(stream, n, Cf, n, Ci, n, rel, cws, flag) != 0) throw Fail{MPSGB_EDEVICE, "Cholesky launch"};
+    int hflag = 0;
+    cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    synchronize("Cholesky");
+    if (hflag) {
+      stats.chol_fallbacks++;
+      ar.off = save;
+      return nullptr;
+    }
+    stats.chol_ok++;
+    ar.off = mark;  // keep Cf and Ci, release the scratch
+    return Cf;
+  }
+
+  // Truncation core with the Cholesky factor of G (G = C C^H, Gs = C): H = C^H E C, new left
+  // isometry C^{-H} V_k, carry (C V_k)^H / sqrt(kept).  Returns false, leaving G untouched, if G is
+  // numerically singular (a pivot at or below 32 eps G_jj); the eigenvector factor then handles it.
+  bool core_chol(int r2, int kcap, C* G, C* E, C* WL, C* Kc, int& k, double& kept, double& total) {
+    const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+    const size_t save = ar.off;
+    C* Ci = nullptr;
+    C* Cf = try_chol(r2, G, Ci);
+    if (!Cf) return false;
+    C* T1 = ar.take<C>((size_t)r2 * r2);
+    C* H = ar.take<C>((size_t)r2 * r2);
+    R* Lam = ar.take<R>(r2);
+    C* V = ar.take<C>((size_t)r2 * r2);
+    if (!V) throw Fail{MPSGB_ENOMEM, "workspace exhausted in truncation core"};
+    gemm<R>(stream, r2, r2, r2, one, rowmajor<R>(E, r2), rowmajor<R>(Cf, r2), zero, rowmajor<R>(T1, r2));
+    gemm<R>(stream, r2, r2, r2, one, transposed<R>(Cf, r2, true), rowmajor<R>(T1, r2), zero, rowmajor<R>(H, r2));
+    const size_t save2 = ar.off;
+    void* ws = ar.take<char>(eigh_workspace_bytes(r2, 1, sizeof(R)));
+    if (!ws) throw Fail{MPSGB_ENOMEM, "workspace exhausted in truncation core"};
+    std::vector<double> hL;
+    eig(r2, H, Lam, V, ws, hL, std::max(1, std::min(kcap, r2)));
+    ar.off = save2;
+    total = 0;
+    for (double x : hL) total += std::max(x, 0.0);
+    k = std::max(1, count_above(hL, tau, kcap));
+    kept = 0;
+    for (int i = 0; i < k; ++i) kept += std::max(hL[i], 0.0);
+    if (!(kept > 0) || !(total > 0)) throw Fail{MPSGB_ESTATE, "non-positive weight at a truncation"};
+    // WL = C^{-H} V[:, :k]
+    gemm<R>(stream, r2, k, r2, one, transposed<R>(Ci, r2, true), rowmajor<R>(V, r2), zero, rowmajor<R>(WL, k));
+    // Kc = V_k^H C^H / sqrt(kept)
+    View<R> vkh; vkh.ptr = V; vkh.row = plain(1); vkh.col = plain(r2); vkh.conj = true;
+    gemm<R>(stream, k, r2, r2, cmake<R>((R)(1.0 / std::sqrt(kept)), 0), vkh, transposed<R>(Cf, r2, true), zero,
+            rowmajor<R>(Kc, r2));
+    ar.off = save;
+    return true;
   }
 
   // ---------------------------------------------------------- inter-block gate
@@ -684,7 +861,8 @@ class EngineT : public Engine {
       env_assemble<R>(stream, r, E00[m], E01[m], E);
       int k = 0;
       double kept = 0, total = 0;
-      core(r2, rows, cap_bond(m), G, E, WL, nextK, k, kept, total);
+      // G is block diagonal at m = p (two halves of rows / 2 rows each): full rank needs rows / 2 >= r
+      core(r2, rows, cap_bond(m), G, E, WL, nextK, k, kept, total, m == p ? rows / 2 >= r : rows >= r2);
       // new left-isometric block m
       if (m == p) {
         for (int v = 0; v < 2; ++v) {

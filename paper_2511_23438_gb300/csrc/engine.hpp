@@ -34,6 +34,8 @@ struct Stats {
   long long centre_moves = 0;
   long long eig_calls = 0;
   long long eig_sweeps = 0;
+  long long chol_ok = 0;         // Gram matrices factorised by Cholesky
+  long long chol_fallbacks = 0;  // ... that were too close to singular (eigenvector factor taken instead)
 };
 
 class Engine {

@@ -10,6 +10,8 @@
 
 namespace mpsgb {
 
+thread_local int g_gemm_site = KT_GEMM;
+
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16;  // tile of the real split-K GEMM below
 
@@ -170,15 +172,15 @@ void gemm_splitk(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, V
   const int kchunk = ((K + splits - 1) / splits + CK - 1) / CK * CK;
   splits = (K + kchunk - 1) / kchunk;
   View<R> W = rowmajor<R>(ws, N);
-  kt_begin(KT_GEMM, st);
+  kt_begin(g_gemm_site, st);
   dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
   cgemm_kernel<R, 4><<<grid, 256, 0, st>>>(M, N, K, cmake<R>(1, 0), A, B, cmake<R>(0, 0), W, 0, 0, (long long)M * N,
                                            kchunk);
   const long long tot = (long long)M * N;
   csplit_reduce_kernel<R><<<(unsigned)std::min<long long>((tot + 255) / 256, 1216), 256, 0, st>>>(M, N, splits, alpha,
                                                                                                   ws, beta, C);
-  kt_end(KT_GEMM, st);
-  kt_add_work(KT_GEMM, 8.0 * M * N * (double)K);
+  kt_end(g_gemm_site, st);
+  kt_add_work(g_gemm_site, 8.0 * M * N * (double)K);
   count_launch(2);
 }
 
@@ -195,7 +197,7 @@ void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> 
     scale_view(st, M, N, beta, C, batch, sC);
     return;
   }
-  kt_begin(KT_GEMM, st);
+  kt_begin(g_gemm_site, st);
   // 128 x 128 tiles (FP32) when they alone fill the GPU, else 64 x 64 tiles
   const long long t128 = (long long)((M + 127) / 128) * ((N + 127) / 128) * batch;
   bool big = false;
@@ -210,8 +212,8 @@ void gemm(cudaStream_t st, int M, int N, int K, Cx<R> alpha, View<R> A, View<R> 
     dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
     cgemm_kernel<R, 4><<<grid, 256, 0, st>>>(M, N, K, alpha, A, B, beta, C, sA, sB, sC, 0);
   }
-  kt_end(KT_GEMM, st);
-  kt_add_work(KT_GEMM, 8.0 * M * N * (double)K * batch);
+  kt_end(g_gemm_site, st);
+  kt_add_work(g_gemm_site, 8.0 * M * N * (double)K * batch);
   count_launch();
 }
 
@@ -306,7 +308,7 @@ void rgemm(cudaStream_t st, int M, int N, int K, R alpha, const R* A, long long 
   const int kchunk = splits > 1 ? ((K + splits - 1) / splits + BK - 1) / BK * BK : std::max(K, 1);
   splits = splits > 1 ? (K + kchunk - 1) / kchunk : 1;
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
-  kt_begin(KT_GEMM, st);
+  kt_begin(g_gemm_site, st);
   if (splits == 1) {
     rgemm_kernel<R><<<grid, 256, 0, st>>>(M, N, K, kchunk, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc, 0);
     count_launch();
@@ -319,8 +321,8 @@ void rgemm(cudaStream_t st, int M, int N, int K, R alpha, const R* A, long long 
     count_launch();
     count_launch();
   }
-  kt_end(KT_GEMM, st);
-  kt_add_work(KT_GEMM, 2.0 * M * N * (double)K);
+  kt_end(g_gemm_site, st);
+  kt_add_work(g_gemm_site, 2.0 * M * N * (double)K);
 }
 
 template void rgemm<double>(cudaStream_t, int, int, int, double, const double*, long long, bool, const double*,

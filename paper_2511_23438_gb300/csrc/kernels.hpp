@@ -44,13 +44,25 @@ template <typename R>
 int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R* w, long long sw, Cx<R>* V,
          long long ldv, long long sV, int batch, void* workspace, int nvec = 0);
 
+// ---------------------------------------------------------------- Cholesky (chol.cu)
+// A = C C^H for the n x n Hermitian matrix A (row-major, lda), in place: A becomes the lower-
+// triangular C (strict upper triangle zeroed) and Ci (row-major, ldi) the lower-triangular C^{-1}.
+// ws: chol_workspace_bytes(n).  flag (device int) is set non-zero if a pivot fell to or below
+// rel * A_jj (its column's diagonal): A is then treated as numerically singular.  Returns 0, or -4
+// for a launch error.  Does not synchronise.
+size_t chol_workspace_bytes(int n, int real_bytes);
+template <typename R>
+int chol_inv(cudaStream_t st, int n, Cx<R>* A, long long lda, Cx<R>* Ci, long long ldi, double rel, void* ws,
+             int* flag);
+
 // ---------------------------------------------------------------- Jacobi SVD (svd.cu)
 // SVD of `batch` p x q complex matrices X (row-major, leading dim ldx, batch stride sX; read only) by
 // one-sided Jacobi rotations of the rows: X = U diag(s) Vh with s descending (FP64, device s and/or
 // host s_host, either may be null), Vh (p x q, orthonormal rows where s > 0, zero rows where s == 0)
 // and U (p x p, unitary); Vh or U may be null.  Returns the number of sweeps, -1 if the sweep limit
-// was reached, -2 if a bounded grid barrier timed out, -4 for a launch or device error.  Synchronises
-// the stream.
+// was reached, -2 if a bounded grid barrier timed out, -4 for a launch or device error, -5 if a
+// singular value came out non-finite (non-finite input; s_host must be given to detect it).
+// Synchronises the stream.
 size_t svd_rows_workspace_bytes(int p, int q, int batch, int real_bytes);
 template <typename R>
 int svd_rows(cudaStream_t st, int p, int q, const Cx<R>* X, long long ldx, double* s, double* s_host, Cx<R>* Vh,
@@ -65,6 +77,10 @@ void mpo_expand(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* in,
 // X[i, :cols] *= c s[i] for i < rows (s: device FP64)
 template <typename R>
 void scale_rows(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c);
+// theta (l, da, db, r) *= exp(-i phi z_a z_b), z_a = 1 - 2 bit shift_a of the first physical index,
+// z_b likewise of the second (the gate of a two-site update)
+template <typename R>
+void two_site_phase(cudaStream_t st, int l, int da, int db, int r, Cx<R>* th, double phi, int shift_a, int shift_b);
 // X[:rows, j] *= c s[j] for j < cols (s: device FP64)
 template <typename R>
 void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c);

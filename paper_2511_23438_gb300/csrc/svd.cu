@@ -201,21 +201,24 @@ __global__ void rank_sort_kernel(int p, const double* nrm, int* perm, double* s_
   s_sorted += (long long)prob * p;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p) return;
-  const double v = nrm[i];
+  // a total order (a non-finite norm counts as -1, below every norm, ties by row) so that the
+  // ranks are always a permutation of 0 .. p-1; the host rejects non-finite norms afterwards
+  auto key = [](double x) { return isfinite(x) ? x : -1.0; };
+  const double v = key(nrm[i]);
   int rank = 0;
   for (int j = 0; j < p; ++j) {
-    const double u = nrm[j];
+    const double u = key(nrm[j]);
     rank += (u > v) || (u == v && j < i);
   }
   perm[rank] = i;
-  s_sorted[rank] = v;
+  s_sorted[rank] = nrm[i];
 }
 
 // Vh[i, :] = X[perm[i], :] / s_i (zero row where s_i == 0); U[r, i] = conj(J[perm[i], r])
 template <typename R>
 __global__ void svd_finish_kernel(int p, int q, const Cx<R>* X, long long ldx, long long sX, const Cx<R>* J,
                                   long long ldj, long long sJ, const int* perm, const double* s, Cx<R>* Vh,
-                                  long long ldvh, long long sVh, Cx<R>* U, long long ldu, long long sU) {
+                                  long long ldvh, long long sVh, Cx<R>* U, long long ldu, long long sU, int* err) {
   const int prob = blockIdx.y;
   X += prob * sX; J += prob * sJ; Vh += prob * sVh; U += prob * sU;
   perm += (long long)prob * p;
@@ -226,15 +229,19 @@ __global__ void svd_finish_kernel(int p, int q, const Cx<R>* X, long long ldx, l
     if (e < totv) {
       if (!Vh) continue;
       const long long i = e / q, j = e - i * q;
+      const int pi = perm[i];
+      if (pi < 0 || pi >= p) { atomicExch(err, 2); continue; }  // never taken: perm is a permutation
       const double si = s[i];
-      const Cx<R> x = X[(long long)perm[i] * ldx + j];
+      const Cx<R> x = X[(long long)pi * ldx + j];
       const R f = si > 0 ? (R)(1.0 / si) : R(0);
       Vh[i * ldvh + j] = f * x;
     } else {
       if (!U) continue;
       const long long f2 = e - totv;
       const long long r = f2 / p, i = f2 - r * p;
-      U[r * ldu + i] = conj(J[(long long)perm[i] * ldj + r]);
+      const int pi = perm[i];
+      if (pi < 0 || pi >= p) { atomicExch(err, 2); continue; }
+      U[r * ldu + i] = conj(J[(long long)pi * ldj + r]);
     }
   }
 }
@@ -275,6 +282,21 @@ __global__ void mpo_expand_kernel(int mode, int l, int d, int r, const Cx<R>* in
     else if (mode == 1) y = v == w ? x : cmake<R>(0, 0);
     else y = v == 0 ? x : (R)z * x;
     out[e] = y;
+  }
+}
+
+// theta[(a, s), (t, b)] *= exp(-i phi z(s, shift_a) z(t, shift_b)), z(x, k) = 1 - 2 bit_k(x)
+template <typename R>
+__global__ void two_site_phase_kernel(int l, int da, int db, int r, Cx<R>* th, double phi, int shift_a, int shift_b) {
+  const long long tot = (long long)l * da * db * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long ab = e / r;
+    const int t = (int)(ab % db);
+    const int s = (int)((ab / db) % da);
+    const double z = (((s >> shift_a) & 1) ? -1.0 : 1.0) * (((t >> shift_b) & 1) ? -1.0 : 1.0);
+    double sn, cs;
+    sincos(phi * z, &sn, &cs);
+    th[e] = cmake<R>((R)cs, (R)(-sn)) * th[e];
   }
 }
 
@@ -344,7 +366,9 @@ int svd_rows(cudaStream_t st, int p, int q, const Cx<R>* X, long long ldx, doubl
     copy_view<R, R>(st, p, q, rowmajor<R>(const_cast<Cx<R>*>(X) + b * sX, ldx), rowmajor<R>(Xw + (size_t)b * p * q, q));
   identity_batch_kernel<R><<<dim3(grid_of((long long)p * p, 256), batch), 256, 0, st>>>(p, Jw, p, (long long)p * p);
   count_launch();
+  const double eps = sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920929e-7;
   if (batch == 1 && p >= 2) {
+    double top0 = 0;
     Cx<R>* G = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)p * p * 2));
     Cx<R>* V = G + (size_t)p * p;
     R* w = reinterpret_cast<R*>(take(sizeof(R) * (size_t)p));
@@ -360,21 +384,24 @@ int svd_rows(cudaStream_t st, int p, int q, const Cx<R>* X, long long ldx, doubl
       gemm<R>(st, m, m, q, one, rowmajor<R>(Xs, q), transposed<R>(Xs, q, true), zero, rowmajor<R>(G, m));
       const int es = eigh<R>(st, m, G, m, 0, w, 0, V, m, 0, 1, eigws);
       if (es == -2) return -2;
-      if (es < 0) return -4;
+      if (es == -4) return -4;
+      if (es < 0) break;  // no usable eigenvectors for this level: the sweeps start from here
+      cudaMemcpyAsync(hw.data(), w, sizeof(R) * m, cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
+      // rows at the rounding floor of the first level (or a Gram that is not finite) carry no
+      // direction worth rotating to: the sweeps start from here
+      if (level == 0) top0 = (double)hw[0];
+      if (!std::isfinite((double)hw[0]) || !((double)hw[0] > 64.0 * eps * eps * top0)) break;
       gemm<R>(st, m, q, m, one, transposed<R>(V, m, true), rowmajor<R>(Xs, q), zero, rowmajor<R>(T, q));
       cudaMemcpyAsync(Xs, T, sizeof(Cx<R>) * (size_t)m * q, cudaMemcpyDeviceToDevice, st);
       gemm<R>(st, m, p, m, one, transposed<R>(V, m, true), rowmajor<R>(Js, p), zero, rowmajor<R>(T, p));
       cudaMemcpyAsync(Js, T, sizeof(Cx<R>) * (size_t)m * p, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(hw.data(), w, sizeof(R) * m, cudaMemcpyDeviceToHost, st);
-      if (cudaStreamSynchronize(st) != cudaSuccess) return -4;
-      if (!(hw[0] > 0)) break;
       int t = 0;
       while (t < m && (double)hw[t] > 1e-6 * (double)hw[0]) ++t;
       if (t == 0 || t >= m - 1) break;
       start += t;
     }
   }
-  const double eps = sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920929e-7;
   const double tol = eps * std::sqrt((double)std::max(q, 16));
   const long long lim = wait_limit_cycles();
   // one CTA per problem unless a single large problem can use the whole GPU
@@ -408,7 +435,8 @@ int svd_rows(cudaStream_t st, int p, int q, const Cx<R>* X, long long ldx, doubl
   row_norms_kernel<R><<<dim3((p + 7) / 8, batch), 256, 0, st>>>(p, q, Xw, q, (long long)p * q, nrm);
   rank_sort_kernel<<<dim3((p + 127) / 128, batch), 128, 0, st>>>(p, nrm, perm, nrm + (size_t)p * batch);
   svd_finish_kernel<R><<<dim3(grid_of((long long)p * (p + q), 256), batch), 256, 0, st>>>(
-      p, q, Xw, q, (long long)p * q, Jw, p, (long long)p * p, perm, nrm + (size_t)p * batch, Vh, ldvh, sVh, U, ldu, sU);
+      p, q, Xw, q, (long long)p * q, Jw, p, (long long)p * p, perm, nrm + (size_t)p * batch, Vh, ldvh, sVh, U, ldu, sU,
+      err);
   count_launch(3);
   if (s) cudaMemcpyAsync(s, nrm + (size_t)p * batch, sizeof(double) * (size_t)p * batch, cudaMemcpyDeviceToDevice, st);
   if (s_host)
@@ -418,7 +446,11 @@ int svd_rows(cudaStream_t st, int p, int q, const Cx<R>* X, long long ldx, doubl
   cudaMemcpyAsync(hs.data(), sweeps, sizeof(int) * batch, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return -4;
+  if (herr == 2) return -4;  // a bad permutation was caught (see svd_finish_kernel)
   if (herr) return -2;
+  if (s_host)
+    for (int i = 0; i < p * batch; ++i)
+      if (!std::isfinite(s_host[i])) return -5;  // the input was not finite
   int mx = 0;
   for (int v : hs) {
     if (v < 0) return -1;
@@ -441,6 +473,13 @@ void scale_rows(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, con
 }
 
 template <typename R>
+void two_site_phase(cudaStream_t st, int l, int da, int db, int r, Cx<R>* th, double phi, int shift_a, int shift_b) {
+  two_site_phase_kernel<R><<<grid_of((long long)l * da * db * r, 256), 256, 0, st>>>(l, da, db, r, th, phi, shift_a,
+                                                                                    shift_b);
+  count_launch();
+}
+
+template <typename R>
 void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c) {
   scale_cols_kernel<R><<<grid_of((long long)rows * cols, 256), 256, 0, st>>>(rows, cols, X, ld, s, c);
   count_launch();
@@ -451,7 +490,8 @@ void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, con
                            Cx<R>*, long long, void*, int, long long, long long, long long);                         \
   template void mpo_expand<R>(cudaStream_t, int, int, int, int, const Cx<R>*, Cx<R>*, double, int);                 \
   template void scale_rows<R>(cudaStream_t, int, int, Cx<R>*, long long, const double*, double);              \
-  template void scale_cols<R>(cudaStream_t, int, int, Cx<R>*, long long, const double*, double);
+  template void scale_cols<R>(cudaStream_t, int, int, Cx<R>*, long long, const double*, double);             \
+  template void two_site_phase<R>(cudaStream_t, int, int, int, int, Cx<R>*, double, int, int);
 MPSGB_SVD_INST(double)
 MPSGB_SVD_INST(float)
 

@@ -89,11 +89,13 @@ int mpsgb_kernel_times(int site, double* ms, long long* launches, double* work) 
 }
 
 const char* mpsgb_kernel_site_name(int site) {
-  static const char* names[] = {"cgemm (CUDA-core complex GEMM)", "jacobi pair solve", "jacobi rotation update",
+  static const char* names[] = {"cgemm (CUDA-core complex GEMM: truncation core, contractions)", "jacobi pair solve", "jacobi rotation update",
                                 "jacobi small (n<=32)", "in-block gate (apply_phys)", "tcgen05 split GEMM",
                                 "Householder tridiagonal reduction (hetrd)",
                                 "tridiagonal eigenvectors (bisection, inverse iteration, cluster GS)",
-                                "one-sided Jacobi SVD (exact truncation route)"};
+                                "one-sided Jacobi SVD (exact truncation route)",
+                                "cgemm inside the eigensolver (orthonormalisation, back-transformation)",
+                                "cgemm of the Cholesky factorisation and solves"};
   if (site < 0 || site >= mpsgb::KT_NSITES) return "";
   return names[site];
 }

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -49,39 +50,81 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned target, int*
   __syncthreads();
 }
 
+// Split form of grid_sync: grid_arrive publishes this CTA's writes and counts it in; grid_wait
+// (after independent work) waits until `target` arrivals, bounded like grid_sync.
+__device__ __forceinline__ void grid_arrive(unsigned* count) {
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+}
+__device__ __forceinline__ void grid_wait(unsigned* count, unsigned target, int* err, long long lim) {
+  if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    unsigned v;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (clock64() - t0 > lim) { atomicExch(err, 1); break; }
+    }
+  }
+  __syncthreads();
+}
+
 // Householder reduction of the Hermitian n x n matrix A to real symmetric tridiagonal form.
-// Rows of the working copy W are owned cyclically by the CTAs.  Per column i:
-//   A. every CTA forms the reflector (beta, tau, v) of column i itself, v kept in shared memory;
-//      owned rows: p_r = tau (W22 v)_r (one warp per row) and a partial p^H v;      barrier 1
+// Rows of the working matrix are owned cyclically by the CTAs (CTA c: rows c, c + G, ...; slot t
+// holds row c + t G).  A CTA keeps its rows in shared memory except the first T0 slots when not
+// all fit; those rows stay in the global copy W, and as the lowest-numbered rows they drop out of
+// the active trailing matrix first (after column c + (T0 - 1) G).  Per column i:
+//   A. every CTA forms the reflector (beta, tau, v) of column i itself from the contiguous copy of
+//      column i in colbuf (parity i & 1), v kept in shared memory; owned rows: p_r = tau (W22 v)_r
+//      (one warp per row) and a partial p^H v; arrive at barrier 1, apply the part -p_r conj(v_j)
+//      of the update that needs only the CTA's own p_r, wait at barrier 1;
 //   B. every CTA loads p into shared memory; owned rows: W22 -= v w^H + w v^H with
-//      w = p - (tau/2)(p^H v) v; the Householder vector is stored in column i; the squared
-//      norm of the next column below its sub-diagonal is accumulated.               barrier 2
+//      w = p - (tau/2)(p^H v) v, column i+1 first: it goes to colbuf (other parity), its squared
+//      norm below the sub-diagonal is accumulated, the owner of row i+1 writes d[i+1], and the
+//      CTA arrives at barrier 2; then the rest of its rows (columns i+2 ..), the Householder
+//      vector into column i of W (global) for the back-transformation, and the wait on
+//      barrier 2, whose latency the update hides (the next column only needs colbuf).
 // acc[0..1]: squared norm of column i (parity i & 1); acc[2..5]: p^H v (re, im) by parity.
 template <typename R>
 __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long long lda, Cx<R>* W, R* d, R* e,
-                                                    Cx<R>* tau, Cx<R>* pb, double* acc, unsigned* bar, int* err,
-                                                    long long lim) {
+                                                    Cx<R>* tau, Cx<R>* pb, Cx<R>* colbuf, double* acc, unsigned* bar,
+                                                    int* err, long long lim, int s_fit) {
   extern __shared__ __align__(16) unsigned char hetrd_smem[];
   __shared__ double hsc[6];  // tau (re, im), 1 / (alpha - beta) (re, im), a2 (re, im)
   Cx<R>* vs = reinterpret_cast<Cx<R>*>(hetrd_smem);
   Cx<R>* ps = vs + n;
+  Cx<R>* rs = ps + n;  // s_fit cached rows
   const int G = gridDim.x, c = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
   const int warp = t >> 5, lane = t & 31, nw = nt >> 5;
+  const int nslots = c < n ? (n - c + G - 1) / G : 0;
+  const int T0 = nslots > s_fit ? nslots - s_fit : 0;
+  auto rowp = [&](int slot) -> Cx<R>* {
+    return slot >= T0 ? rs + (long long)(slot - T0) * n : W + (long long)(c + slot * G) * n;
+  };
   unsigned nbar = 0;
   double nrm = 0;
-  for (int r = c; r < n; r += G) {
-    for (int j = t; j < n; j += nt) W[(long long)r * n + j] = A[(long long)r * lda + j];
-    if (r >= 2 && t == 0) nrm += (double)abs2(A[(long long)r * lda]);
+  for (int slot = 0; slot < nslots; ++slot) {
+    const int r = c + slot * G;
+    Cx<R>* dst = rowp(slot);
+    for (int j = t; j < n; j += nt) dst[j] = A[(long long)r * lda + j];
+    if (t == 0) {
+      const Cx<R> a0 = A[(long long)r * lda];
+      colbuf[r] = a0;
+      if (r >= 2) nrm += (double)abs2(a0);
+      if (r == 0) d[0] = a0.x;
+    }
   }
   if (t == 0 && nrm != 0) atomicAdd(&acc[0], nrm);
   grid_sync(bar, (++nbar) * G, err, lim);
   for (int i = 0; i < n - 1; ++i) {
     const int par = i & 1;
+    const Cx<R>* col = colbuf + (size_t)par * n;   // column i, rows >= i + 1
+    Cx<R>* coln = colbuf + (size_t)(par ^ 1) * n;  // column i + 1, written in phase B
     // ---- A: reflector of column i (thread 0 of every CTA forms the same scalars in FP64 and
     // shares them: FP64 divisions and square roots are slow on this part, so they are not
     // repeated by every thread), v into shared memory
     if (t == 0) {
-      const Cx<R> alpha = W[(long long)(i + 1) * n + i];
+      const Cx<R> alpha = col[i + 1];
       const double xn2 = acc[par];
       const double ar = alpha.x, ai = alpha.y;
       double beta, tr, ti, sr = 0, si = 0;
@@ -98,7 +141,6 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
       }
       hsc[0] = tr; hsc[1] = ti; hsc[2] = sr; hsc[3] = si;
       if (c == 0) {
-        d[i] = W[(long long)i * n + i].x;
         e[i] = (R)beta;
         tau[i] = cmake<R>((R)tr, (R)ti);
       }
@@ -106,15 +148,15 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
     __syncthreads();
     const Cx<R> tv = cmake<R>((R)hsc[0], (R)hsc[1]);
     const Cx<R> scale = cmake<R>((R)hsc[2], (R)hsc[3]);
-#pragma unroll 4
-    for (int j = i + 1 + t; j < n; j += nt) vs[j] = j == i + 1 ? cmake<R>(1, 0) : scale * W[(long long)j * n + i];
+    for (int j = i + 1 + t; j < n; j += nt) vs[j] = j == i + 1 ? cmake<R>(1, 0) : scale * col[j];
     __syncthreads();
-    const int r0 = i + 1 + ((c - (i + 1)) % G + G) % G;
+    const int s0 = i + 1 <= c ? 0 : (i + 1 - c + G - 1) / G;  // first slot with a row >= i + 1
     {
       double dre = 0, dim = 0;
-      for (int r = r0 + warp * G; r < n; r += nw * G) {
+      for (int slot = s0 + warp; slot < nslots; slot += nw) {
+        const int r = c + slot * G;
+        const Cx<R>* row = rowp(slot);
         Cx<R> sacc = cmake<R>(0, 0);
-        const Cx<R>* row = W + (long long)r * n;
 #pragma unroll 16
         for (int j = i + 1 + lane; j < n; j += 32) cfma(sacc, row[j], vs[j]);
         R sr = sacc.x, si = sacc.y;
@@ -125,6 +167,7 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
         if (lane == 0) {
           const Cx<R> pv = tv * cmake<R>(sr, si);
           pb[r] = pv;
+          ps[r] = pv;
           const Cx<R> v = vs[r];
           dre += (double)pv.x * v.x + (double)pv.y * v.y;  // conj(p) v
           dim += (double)pv.x * v.y - (double)pv.y * v.x;
@@ -135,7 +178,43 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
         atomicAdd(&acc[3 + 2 * par], dim);
       }
     }
-    grid_sync(bar, (++nbar) * G, err, lim);
+    // The update W22 -= v w^H + w v^H, w = p + a2 v, splits into the local part -p_r conj(v_j) of
+    // an owned row r and the part -v_r conj(p_j + 2 Re(a2) v_j) that needs every p_j and the
+    // reduced p^H v.  The local part is applied while the other CTAs reach barrier 1.
+    grid_arrive(bar);
+    ++nbar;
+    for (int sb = s0; sb < nslots; sb += 4) {
+      Cx<R>* rp[4];
+      Cx<R> pr[4];
+      bool ok[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int slot = sb + q;
+        ok[q] = slot < nslots;
+        rp[q] = rowp(ok[q] ? slot : sb);
+        pr[q] = ok[q] ? ps[c + slot * G] : cmake<R>(0, 0);
+      }
+      for (int j0 = i + 1 + t; j0 < n; j0 += 4 * nt) {
+        Cx<R> x[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * nt;
+            if (ok[q] && j < n) x[q][u] = rp[q][j];
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * nt;
+          if (j >= n) break;
+          const Cx<R> cvj = conj(vs[j]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (ok[q]) rp[q][j] = x[q][u] - pr[q] * cvj;
+        }
+      }
+    }
+    grid_wait(bar, nbar * G, err, lim);
     // ---- B: rank-2 update of the owned rows
     for (int j = i + 1 + t; j < n; j += nt) ps[j] = pb[j];
     if (t == 0) {  // a2 = -tau (p^H v) / 2
@@ -149,51 +228,62 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
       }
     }
     __syncthreads();
-    const Cx<R> a2 = cmake<R>((R)hsc[4], (R)hsc[5]);
-    double nn = 0;
-    // owned rows four at a time, four column strides per pass: up to 16 independent loads per thread
-    for (int rb = r0; rb < n; rb += 4 * G) {
-      Cx<R>* rowp[4];
-      Cx<R> vr[4], wr[4];
+    const R ra2 = (R)(2.0 * hsc[4]);  // 2 Re(a2)
+    {  // column i + 1 of the owned rows (one thread per row), then arrive
+      double nn = 0;
+      const Cx<R> uj = conj(ps[i + 1] + ra2 * vs[i + 1]);
+      for (int slot = s0 + t; slot < nslots; slot += nt) {
+        const int r = c + slot * G;
+        Cx<R>* row = rowp(slot);
+        const Cx<R> y = row[i + 1] - vs[r] * uj;
+        row[i + 1] = y;
+        coln[r] = y;
+        if (r >= i + 3) nn += (double)abs2(y);
+        if (r == i + 1) d[i + 1] = y.x;
+      }
+      if (nn != 0) atomicAdd(&acc[par ^ 1], nn);
+    }
+    grid_arrive(bar);
+    ++nbar;
+    // columns i + 2 .. of the owned rows, four rows at a time, four column strides per pass
+    for (int sb = s0; sb < nslots; sb += 4) {
+      Cx<R>* rp[4];
+      Cx<R> vr[4];
       bool ok[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int r = rb + q * G;
-        ok[q] = r < n;
-        rowp[q] = W + (long long)(ok[q] ? r : rb) * n;
+        const int slot = sb + q;
+        ok[q] = slot < nslots;
+        const int r = c + (ok[q] ? slot : sb) * G;
+        rp[q] = rowp(ok[q] ? slot : sb);
         vr[q] = ok[q] ? vs[r] : cmake<R>(0, 0);
-        wr[q] = ok[q] ? ps[r] + a2 * vr[q] : cmake<R>(0, 0);
-        if (t == 0 && ok[q] && r > i + 1) rowp[q][i] = vr[q];  // Householder vector for the back-transformation
+        // Householder vector for the back-transformation (global copy)
+        if (t == 0 && ok[q] && r > i + 1) W[(long long)r * n + i] = vr[q];
       }
-      for (int j0 = i + 1 + t; j0 < n; j0 += 4 * nt) {
+      for (int j0 = i + 2 + t; j0 < n; j0 += 4 * nt) {
         Cx<R> x[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int j = j0 + u * nt;
-            if (ok[q] && j < n) x[q][u] = rowp[q][j];
+            if (ok[q] && j < n) x[q][u] = rp[q][j];
           }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = j0 + u * nt;
           if (j >= n) break;
-          const Cx<R> vj = vs[j];
-          const Cx<R> wj = ps[j] + a2 * vj;
+          const Cx<R> uj = conj(ps[j] + ra2 * vs[j]);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             if (!ok[q]) continue;
-            const Cx<R> y = x[q][u] - vr[q] * conj(wj) - wr[q] * conj(vj);
-            rowp[q][j] = y;
-            if (j == i + 1 && rb + q * G >= i + 3) nn += (double)abs2(y);
+            rp[q][j] = x[q][u] - vr[q] * uj;
           }
         }
       }
     }
-    if (nn != 0) atomicAdd(&acc[par ^ 1], nn);
-    grid_sync(bar, (++nbar) * G, err, lim);
+    grid_wait(bar, nbar * G, err, lim);
   }
-  if (c == 0 && t == 0) d[n - 1] = W[(long long)(n - 1) * n + (n - 1)].x;
 }
 
 // number of eigenvalues of T smaller than x (Sturm sequence with a pivot floor)
@@ -503,6 +593,7 @@ size_t tri_workspace_bytes(int n, int real_bytes) {
   b += 5 * nn * real_bytes;      // Z, U0, U1, U2, L
   b += nn;                       // pivots
   b += 8 * (size_t)n * c;        // d, e, tau, v, p, w, cluster bounds
+  b += 2 * (size_t)n * c + 256;  // column buffer of the reduction (two parities)
   b += 6 * (size_t)n * 8 + 8 * 256;  // block eigenvalues, block bounds, permutation, cluster lists
   b += 3 * 32 * (size_t)n * c + 2 * 32 * 32 * c + 7 * 256;  // WY panel, Y1, Y2, S, T
   b += (size_t)(8 + 1) * n * 64 * (c / 2) + 2 * 64 * 64 * (c / 2) + 5 * 256;  // real orthonormalisation
@@ -531,6 +622,7 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   R* ev = reinterpret_cast<R*>(take(sizeof(R) * n));
   Cx<R>* tau = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * n));
   Cx<R>* pb = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * n));
+  Cx<R>* colbuf = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * 2 * (size_t)n));
   Cx<R>* Pn = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * (size_t)n * 32));
   Cx<R>* Sm = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * 32 * 32));
   Cx<R>* Tm = reinterpret_cast<Cx<R>*>(take(sizeof(Cx<R>) * 32 * 32));
@@ -561,18 +653,29 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t hsm = 2 * sizeof(Cx<R>) * (size_t)n;  // v and p of the current column
-  if (hsm > 200 * 1024) return -4;
-  if (hsm > 48 * 1024 &&
-      cudaFuncSetAttribute(hetrd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm) != cudaSuccess)
-    return -4;
+  // shared memory: v and p of the current column plus as many owned rows as fit
+  const size_t row_bytes = sizeof(Cx<R>) * (size_t)n;
+  const size_t smem_cap = 220 * 1024;
+  if (2 * row_bytes > smem_cap) return -4;
+  int grid = sms;
+  const int slots = (n + grid - 1) / grid;
+  int s_fit = (int)std::min<size_t>((size_t)slots, (smem_cap - 2 * row_bytes) / row_bytes);
+  const size_t hsm = (2 + (size_t)s_fit) * row_bytes;
+  // the attribute is a property of the kernel, shared by every host thread: it is raised once to
+  // the largest size any launch uses (setting it per launch would race between handles)
+  static std::once_flag attr_once;
+  static bool attr_ok = false;
+  std::call_once(attr_once, [smem_cap] {
+    attr_ok = cudaFuncSetAttribute(hetrd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap) ==
+              cudaSuccess;
+  });
+  if (!attr_ok || hsm > smem_cap) return -4;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hetrd_kernel<R>, 512, hsm);
   if (per_sm < 1) return -4;
-  int grid = sms;
   int n_ = n;
   long long lda_ = lda;
   long long lim = wait_limit_cycles();
-  void* args[] = {&n_, (void*)&A, &lda_, &Wm, &dv, &ev, &tau, &pb, &acc, &bar, &d_err, &lim};
+  void* args[] = {&n_, (void*)&A, &lda_, &Wm, &dv, &ev, &tau, &pb, &colbuf, &acc, &bar, &d_err, &lim, &s_fit};
   kt_begin(KT_HETRD, st);
   if (cudaLaunchCooperativeKernel((void*)hetrd_kernel<R>, dim3(grid), dim3(512), args, hsm, st) != cudaSuccess) return -4;
   kt_end(KT_HETRD, st);

@@ -65,6 +65,8 @@ _SIGS = {
     "mpsgb_last_error": (ctypes.c_char_p, []),
     "mpsgb_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "mpsgb_launch_count": (ctypes.c_ulonglong, []),
+    "mpsgb_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
     "mpsgb_set_wait_limit": (ctypes.c_longlong, [ctypes.c_longlong]),
     "mpsgb_schedule_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
     "mpsgb_schedule_gates": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -245,7 +247,7 @@ def launch_count():
     return load().mpsgb_launch_count()
 
 
-KERNEL_SITES = 9
+KERNEL_SITES = 11
 
 
 def kernel_timing(enable):
@@ -340,11 +342,20 @@ class MPS:
         _check(load().mpsgb_stats(self.h, out))
         return dict(zip(("truncations", "gates", "centre_moves", "eig_calls", "eig_sweeps"), list(out)))
 
+    def counters(self):
+        """All counters (mpsgb_counters): truncations, gates, centre moves, eigensolver / SVD calls and
+        sweeps, Cholesky factorisations and Cholesky fallbacks."""
+        out = (ctypes.c_longlong * 16)()
+        n = ctypes.c_int()
+        _check(load().mpsgb_counters(self.h, out, 16, ctypes.byref(n)))
+        keys = ("truncations", "gates", "centre_moves", "eig_calls", "eig_sweeps", "chol_ok", "chol_fallbacks")
+        return dict(zip(keys, list(out)[: n.value]))
+
     def save(self, path):
         _check(load().mpsgb_save(self.h, path.encode()))
 
 
-def batch_step(mps_list, nsteps, flags=0):
+def batch_step(mps_list, nlayers, use_graph=0):
     arr = (ctypes.c_void_p * len(mps_list))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
                                               for m in mps_list])
-    _check(load().mpsgb_batch_step(arr, len(mps_list), nsteps, flags))
+    _check(load().mpsgb_batch_step(arr, len(mps_list), nlayers, use_graph))

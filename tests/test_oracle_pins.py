@@ -269,6 +269,77 @@ def test_mps_gate_truncation_equals_bruteforce(gate_idx):
     assert np.allclose(m.fidelities, fs, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("gate_idx", [3, 6, 10, 12])
+def test_mps_swap_route_equals_bruteforce(gate_idx):
+    # brute force of SWAP routing on the dense vector (axes = MPS positions): move block q left by
+    # exchanging neighbouring axes, truncating the bond between them after each exchange by the SVD
+    # of the whole reshaped vector, apply the phase to the adjacent pair, truncate that bond, and
+    # exchange back with truncation.  Block distance k gives 2 (k - 1) + 1 truncations.
+    Lx, Ly, chi = 3, 4, 6
+    m = _random_canonical_mps(Lx, Ly, [4, 10, 12, 10, 4], seed=100 + gate_idx)
+    m.chi = chi
+    _, inter = layout.schedule(Lx, Ly)
+    g = inter[gate_idx]
+    p, q, _, _, ti, tj = g
+    ds = [b["d"] for b in m.layout]
+    psi = _dense_mps_order(m).reshape(ds)
+    order = list(range(len(ds)))  # which original block sits at each position
+    phi = -0.25
+    fs = []
+
+    def truncate(psi, bond):
+        dims = psi.shape
+        left = int(np.prod(dims[: bond + 1]))
+        M = psi.reshape(left, -1)
+        U, s, Vh = np.linalg.svd(M, full_matrices=False)
+        k = min(chi, int(np.count_nonzero(s > s[0] * max(M.shape) * np.finfo(float).eps)))
+        fs.append(np.sum(s[:k] ** 2) / np.sum(s ** 2))
+        return ((U[:, :k] * (s[:k] / np.sqrt(np.sum(s[:k] ** 2)))) @ Vh[:k]).reshape(dims)
+
+    def exchange(psi, pos):
+        perm = list(range(psi.ndim))
+        perm[pos], perm[pos + 1] = perm[pos + 1], perm[pos]
+        order[pos], order[pos + 1] = order[pos + 1], order[pos]
+        return np.transpose(psi, perm)
+
+    for pos in range(q - 1, p, -1):
+        psi = truncate(exchange(psi, pos), pos)
+    assert order[p + 1] == q
+    zi = mps.MPS._zdiag(int(math.log2(ds[p])), ti)
+    zj = mps.MPS._zdiag(int(math.log2(ds[q])), tj)
+    shape = [1] * len(ds)
+    shape[p] = ds[p]
+    zz = zi.reshape(shape)
+    shape = [1] * len(ds)
+    shape[p + 1] = ds[q]
+    psi = truncate(psi * np.exp(-1j * phi * zz * zj.reshape(shape)), p)
+    for pos in range(p + 1, q):
+        psi = truncate(exchange(psi, pos), pos)
+    assert order == list(range(len(ds)))
+    m.zz_inter_swap(g, phi)
+    assert len(m.fidelities) == 2 * (q - p - 1) + 1
+    assert min(m.fidelities) < 0.999  # the route really truncated
+    got = _dense_mps_order(m)
+    assert np.abs(got - psi.reshape(-1)).max() < 1e-12
+    assert np.allclose(m.fidelities, fs, rtol=0, atol=1e-13)
+    assert [b["qubits"] for b in m.layout] == [b["qubits"] for b in layout.blocks(Lx, Ly)]
+
+
+@pytest.mark.parametrize("grid,order", [((3, 4), 1), ((3, 4), 2), ((3, 3), 2)])
+def test_mps_swap_route_exact_chi_equals_statevector(grid, order):
+    # at chi >= every bond bound (also of the permuted chains met while swapping) nothing is cut:
+    # SWAP routing reproduces the state vector like the MPO route
+    Lx, Ly = grid
+    chi = 1 << 12
+    rec, psi = sv.run(Lx, Ly, TH_MID, -1.0, 2.0, 0.25, 3, order=order)
+    r = mps.run(Lx, Ly, chi, TH_MID, -1.0, 2.0, 0.25, 3, order=order, route="swap")
+    for k in ("Z", "Z2", "X"):
+        assert np.abs(r[k] - rec[k]).max() < 1e-10
+    assert abs(r["F"][-1] - 1.0) < 1e-12
+    v = r["mps"].to_statevector()
+    assert abs(np.vdot(psi, v)) ** 2 > 1 - 1e-10
+
+
 def test_mps_observables_and_spectra_against_dense():
     Lx, Ly = 3, 4
     m = _random_canonical_mps(Lx, Ly, [4, 9, 11, 7, 3], seed=7)
