@@ -19,6 +19,7 @@
 // Schmidt values of many magnitudes are badly conditioned mostly through that scaling.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 
 #include "common.cuh"
 #include "kernels.hpp"
@@ -127,22 +128,32 @@ size_t chol_workspace_bytes(int n, int real_bytes) {
   return 2 * (size_t)real_bytes * (size_t)n * (size_t)((n + 1) / 2 + NB) + sizeof(double) * (size_t)n + 512;
 }
 
+// the whole factorisation as one launch sequence (no host decision inside)
 template <typename R>
-int chol_inv(cudaStream_t st, int n, Cx<R>* A, long long lda, Cx<R>* Ci, long long ldi, double rel, void* ws,
-             int* flag) {
-  GemmSite site(KT_GEMM_CHOL);
+int chol_issue(cudaStream_t st, int n, Cx<R>* A, long long lda, Cx<R>* Ci, long long ldi, double rel, void* ws,
+               int* flag) {
   Cx<R>* T = static_cast<Cx<R>*>(ws);
   const long long ldt = (n + 1) / 2 + NB;
   double* thr = reinterpret_cast<double*>(static_cast<char*>(ws) + sizeof(Cx<R>) * (size_t)n * ldt);
-  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return -4;
   diag_thr_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(n, A, lda, rel, thr);
   count_launch();
   if (cudaMemset2DAsync(Ci, sizeof(Cx<R>) * ldi, 0, sizeof(Cx<R>) * n, n, st) != cudaSuccess) return -4;
   chol_rec<R>(st, n, A, lda, Ci, ldi, thr, flag, T, ldt);
   zero_upper_kernel<R><<<blocks_for((long long)n * n), 256, 0, st>>>(n, A, lda);
   count_launch();
-  if (cudaGetLastError() != cudaSuccess) return -4;
   return 0;
+}
+
+template <typename R>
+int chol_inv(cudaStream_t st, int n, Cx<R>* A, long long lda, Cx<R>* Ci, long long ldi, double rel, void* ws,
+             int* flag) {
+  GemmSite site(KT_GEMM_CHOL);
+  // a fixed launch sequence for given sizes and buffers: replayed as a CUDA graph where possible
+  GraphKey key{{1, n, (long long)sizeof(R), (long long)(uintptr_t)A, lda, (long long)(uintptr_t)Ci, ldi,
+                (long long)(uintptr_t)ws, (long long)(uintptr_t)flag, (long long)(rel * 1e18),
+                (long long)(uintptr_t)st, 0}};
+  return replay_or_issue(st, key, [&]() { return chol_issue<R>(st, n, A, lda, Ci, ldi, rel, ws, flag); });
 }
 
 template int chol_inv<float>(cudaStream_t, int, c64*, long long, c64*, long long, double, void*, int*);

@@ -56,7 +56,13 @@ template <typename R> inline View<R> transposed(Cx<R>* p, long long ld, bool cj)
 // Launch accounting: every kernel launch made by the library bumps this counter
 // so callers can report how many of our kernels ran in a timed region.
 extern unsigned long long g_launch_count;
-inline void count_launch(unsigned long long n = 1) { __atomic_add_fetch(&g_launch_count, n, __ATOMIC_RELAXED); }
+// while this thread captures a CUDA graph, launches are counted here instead (they run, and are
+// counted, each time the graph is launched)
+extern thread_local unsigned long long* t_launch_sink;
+inline void count_launch(unsigned long long n = 1) {
+  if (t_launch_sink) *t_launch_sink += n;
+  else __atomic_add_fetch(&g_launch_count, n, __ATOMIC_RELAXED);
+}
 
 // Cycle limit of the library's bounded device waits on other CTAs (grid barriers).  The default
 // (4e9 cycles, about 2 s at 2 GHz) is far above any legitimate wait; a test can lower it through

@@ -1,8 +1,25 @@
 // Host-callable wrappers of the library's CUDA kernels (internal API).
 #pragma once
+#include <functional>
+
 #include "common.cuh"
 
 namespace mpsgb {
+
+// ---------------------------------------------------------------- graph replay (graph.cu)
+// Identity of a fixed launch sequence: what it does (tag), its sizes and its buffers and stream.
+struct GraphKey {
+  long long v[12];
+  bool operator==(const GraphKey& o) const {
+    for (int i = 0; i < 12; ++i)
+      if (v[i] != o.v[i]) return false;
+    return true;
+  }
+};
+// Issue the launch sequence `issue` (which returns 0, or non-zero on a failed call) on st: on a
+// capturable stream it is recorded once per key as a CUDA graph and replayed; otherwise issued
+// directly.  Returns 0, or -4 if a call or the capture failed.
+int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int()>& issue);
 
 // ---------------------------------------------------------------- GEMM (gemm.cu)
 template <typename R>

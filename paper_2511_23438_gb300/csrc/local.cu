@@ -6,6 +6,7 @@
 namespace mpsgb {
 
 unsigned long long g_launch_count = 0;
+thread_local unsigned long long* t_launch_sink = nullptr;
 
 namespace {
 long long g_wait_limit = 4000000000LL;

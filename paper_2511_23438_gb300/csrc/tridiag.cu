@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <mutex>
 #include <vector>
@@ -657,7 +658,10 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   const size_t row_bytes = sizeof(Cx<R>) * (size_t)n;
   const size_t smem_cap = 220 * 1024;
   if (2 * row_bytes > smem_cap) return -4;
-  int grid = sms;
+  // about a dozen rows per CTA, at most one CTA per SM: below n ~ 1800 fewer CTAs take part in each
+  // grid barrier, all their rows fit in shared memory, and the SMs left over can run the
+  // reductions of other handles (other streams) at the same time
+  int grid = std::min(sms, std::max(16, (n + 11) / 12));
   const int slots = (n + grid - 1) / grid;
   int s_fit = (int)std::min<size_t>((size_t)slots, (smem_cap - 2 * row_bytes) / row_bytes);
   const size_t hsm = (2 + (size_t)s_fit) * row_bytes;
@@ -787,8 +791,18 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     // leaves the vectors of well-separated eigenvalues orthogonal to working precision, so they
     // are unchanged; the vectors of close eigenvalues are made orthogonal.
     const int ci_smem = 2 * 64 * 65 * (int)sizeof(R);
-    if (cudaFuncSetAttribute(chol_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem) != cudaSuccess)
-      return -4;
+    static std::once_flag ci_once;
+    static bool ci_ok = false;
+    std::call_once(ci_once, [ci_smem] {
+      ci_ok = cudaFuncSetAttribute(chol_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem) ==
+              cudaSuccess;
+    });
+    if (!ci_ok) return -4;
+    // a fixed launch sequence for given sizes and buffers (all inside the workspace): replayed as a
+    // CUDA graph where possible
+    GraphKey key{{2, n, nvec, (long long)sizeof(R), (long long)(uintptr_t)workspace, (long long)(uintptr_t)V, ldv,
+                  (long long)(uintptr_t)st, 0, 0, 0, 0}};
+    const int bt = replay_or_issue(st, key, [&]() -> int {
     for (int b0 = 0; b0 < nvec; b0 += 64) {
       const int nb = std::min(64, nvec - b0);
       R* Zb = Z + b0;
@@ -825,6 +839,9 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
       gemm<R>(st, m, nvec, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
     }
     copy_view<R, R>(st, n, nvec, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
+    return 0;
+    });
+    if (bt != 0) return -4;
   }
   int cherr = 0;
   cudaMemcpyAsync(&cherr, d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
