@@ -53,7 +53,11 @@ def parse():
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs of the short serving run (0: none)")
     ap.add_argument("--serve-steps", type=int, default=3, help="Trotter steps per serving job")
     ap.add_argument("--batch-mps", type=int, default=32, help="MPS of the batched-advance leg (0: none)")
+    ap.add_argument("--three-d", default="3x3x4", help="open 3D grid of the one-qubit-per-site leg ('' : none)")
+    ap.add_argument("--three-d-chi", type=int, default=128)
     ap.add_argument("--peaks", action="store_true", help="measure dense matmul rates (torch) and exit")
+    ap.add_argument("--split-error", default="", help="error table of the complex64 forms against the FP64 GPU "
+                    "form: comma-separated chi:steps pairs on the 5x6 grid (e.g. 64:20,256:8), then exit")
     return ap.parse_args()
 
 
@@ -196,19 +200,21 @@ class OracleSample:
 
 def batched_run(lib, count, prec):
     """The batched workload: `count` independent MPS drawn like the batched configuration (grids
-    4x4 .. 6x6, chi uniform over {32, ..., 512}, dtheta uniform in [pi/12, pi/3], seeded), each
-    grown by two untimed Trotter steps; then one step of every MPS is timed twice, handle after
-    handle on one host thread and through mpsgb_batch_step (one host thread and stream per handle,
-    overlapping on the device)."""
+    4x4 .. 6x6, chi uniform over {32, ..., 512}, dtheta uniform in [pi/12, pi/3], seeded), each on
+    a CUDA stream of its own and grown by two untimed Trotter steps; then one step of every MPS is
+    timed twice: handle after handle on one host thread, and through mpsgb_batch_step (one host
+    thread per handle, overlapping on the device, fixed launch sequences replayed as CUDA graphs)."""
+    import torch
     from paper_2511_23438_gb300 import inputs
 
     mix = inputs.batched_mix(count, seed=20261203, prec=prec)
+    streams = [torch.cuda.Stream() for _ in mix]
     ms = []
-    for j in mix:
+    for j, s in zip(mix, streams):
         th = lib.initial_theta(j["J"], j["h"], j["dtheta"])
         cfg = lib.config(j["Lx"], j["Ly"], j["chi"], th, prec=prec, J=j["J"], h=j["h"], dt=j["dt"], order=j["order"])
-        ms.append(lib.MPS(cfg))
-    lib.batch_step(ms, 2)
+        ms.append(lib.MPS(cfg, stream=s.cuda_stream))
+    lib.batch_step(ms, 2, use_graph=1)
 
     def updates():
         return sum(m.stats()["truncations"] for m in ms)
@@ -221,7 +227,7 @@ def batched_run(lib, count, prec):
     t_seq = time.perf_counter() - t0
     u1 = updates()
     t0 = time.perf_counter()
-    lib.batch_step(ms, 1)
+    lib.batch_step(ms, 1, use_graph=1)
     for m in ms:
         m.observables()
     t_bat = time.perf_counter() - t0
@@ -231,8 +237,37 @@ def batched_run(lib, count, prec):
     return {"mps": count, "precision": prec, "sequential_bond_updates_per_s": (u1 - u0) / t_seq,
             "batched_bond_updates_per_s": (u2 - u1) / t_bat, "sequential_s": t_seq, "batched_s": t_bat,
             "bond_updates_per_step": u2 - u1,
-            "workload": "%d MPS, grids 4x4..6x6, chi in {32..512}, dtheta in [pi/12, pi/3], two untimed steps, then "
-                        "one timed step per MPS (wall clock, host-synchronised)" % count}
+            "workload": "%d MPS, grids 4x4..6x6, chi in {32..512}, dtheta in [pi/12, pi/3], one stream each, two "
+                        "untimed steps, then one timed step per MPS (wall clock, host-synchronised)" % count}
+
+
+def three_d_run(lib, dims, chi, prec, grow=2):
+    """The 3D variant: an open Lx x Ly x Lz cubic grid, one qubit per MPS site (d = 2) along the 3D
+    snake, mid temperature (dtheta = pi/9, theta_min at coordination 6), J = -1, h = 2, dt = 0.25,
+    second order; `grow` untimed steps from the product state, then one step timed with CUDA
+    events on the handle's stream."""
+    import torch
+    Lx, Ly, Lz = (int(v) for v in dims.split("x"))
+    th = lib.initial_theta(J, HX, math.pi / 9, lattice=lib.LATTICE_3D_SITES)
+    s = torch.cuda.Stream()
+    m = lib.MPS(lib.config(Lx, Ly, chi, th, prec=prec, J=J, h=HX, dt=DT, order=2, lattice=lib.LATTICE_3D_SITES, Lz=Lz),
+                stream=s.cuda_stream)
+    m.step(J, HX, DT, 2, grow)
+    u0 = m.stats()["truncations"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    m.step(J, HX, DT, 2, 1)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    u = m.stats()["truncations"] - u0
+    out = {"workload": "3D TFIM %dx%dx%d open grid, one qubit per site (d=2, %d sites), chi=%d, mid temperature "
+                       "(dtheta=pi/9), %d untimed steps then one timed" % (Lx, Ly, Lz, Lx * Ly * Lz, chi, grow),
+           "precision": prec, "bond_updates_per_s": u / (ms / 1e3), "ms_per_step": ms, "bond_updates_per_step": u,
+           "F": m.fidelity(), "max_bond": max(m.bond_dims())}
+    m.close()
+    return out
 
 
 def cpu_baseline(Lx, Ly, chi, n_updates):
@@ -312,6 +347,37 @@ def fp64_form_rate(lib, m_split, Lx, Ly, n_updates, stream):
                       (Lx, Ly, m_split.cfg.chi_max, n)}
 
 
+def split_error_table(spec, prec, Lx=5, Ly=6):
+    """Error of a complex64 form against the FP64 GPU form (both through the library, the FP64
+    form being the one held to 1e-9 of the oracle) on the 5x6 grid (rows 3 + 3, d = 8) from the
+    mid-temperature product state: for each chi, `steps` second-order steps side by side, the
+    largest |d<Z_tot>|, |d<Z_tot^2>|, |d<X_tot>| and |dF/F| over the steps."""
+    from paper_2511_23438_gb300 import lib
+    lib.load()
+    theta = lib.initial_theta(J, HX, TEMP_DTHETA)
+    rows = []
+    for item in spec.split(","):
+        chi, steps = (int(v) for v in item.split(":"))
+        a = lib.MPS(lib.config(Lx, Ly, chi, theta, prec="fp64"))
+        b = lib.MPS(lib.config(Lx, Ly, chi, theta, prec=prec))
+        err = {"Z": 0.0, "Z2": 0.0, "X": 0.0, "F_rel": 0.0}
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            a.step(J, HX, DT, ORDER, 1)
+            b.step(J, HX, DT, ORDER, 1)
+            oa, ob = a.observables(), b.observables()
+            for k in ("Z", "Z2", "X"):
+                err[k] = max(err[k], abs(oa[k] - ob[k]))
+            err["F_rel"] = max(err["F_rel"], abs(b.fidelity() / a.fidelity() - 1))
+        rows.append({"chi": chi, "steps": steps, "F_fp64": a.fidelity(), "max_bond": max(a.bond_dims()),
+                     "max_abs_err": err, "s": time.perf_counter() - t0})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        a.close()
+        b.close()
+    return {"split_error": rows, "precision": prec, "grid": "%dx%d" % (Lx, Ly),
+            "reference": "FP64 GPU form (complex128, exact SVD truncation)"}
+
+
 def reduce_over_ranks(ms, updates, dist, device):
     """Replicas: the job's time is the slowest rank's timed region, its work the sum of all
     ranks' bond updates (no collective touches the data path; this is the only one)."""
@@ -336,6 +402,9 @@ def main():
         return
     if args.peaks:
         print(json.dumps(measure_peaks()), flush=True)
+        return
+    if args.split_error:
+        print(json.dumps(split_error_table(args.split_error, args.prec)), flush=True)
         return
 
     import torch
@@ -483,6 +552,8 @@ def main():
         line["serve"] = serve_run(args.serve_jobs, args.serve_steps, args.prec)
     if args.batch_mps > 0 and world == 1:
         line["batched"] = batched_run(lib, args.batch_mps, args.prec)
+    if args.three_d and world == 1:
+        line["three_d"] = three_d_run(lib, args.three_d, args.three_d_chi, args.prec)
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(Lx, Ly, args.chi, args.cpu_updates)
     print(json.dumps(line), flush=True)

@@ -71,9 +71,24 @@ typedef enum { MPSGB_ROUTE_MPO = 0, MPSGB_ROUTE_SWAP = 1 } mpsgb_route;
 typedef enum { MPSGB_LAYER_X = 0, MPSGB_LAYER_ZZ = 1 } mpsgb_layer;
 typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2 } mpsgb_obs;
 
+/* Lattice and its mapping onto MPS sites.
+ *   LATTICE_2D_GROUPED  the paper's main setting (Sec. II-III, Fig. mps_drawing): an Lx x Ly grid,
+ *                       periodic in both directions; each row split into two groups of ceil(Ly/2)
+ *                       and floor(Ly/2) qubits, each group one MPS block (d = 2^k), blocks along a
+ *                       row snake.  Lz must be 0 or 1.
+ *   LATTICE_3D_SITES    the 3D variant of the Supplemental Material (section "3D Transverse Field
+ *                       Ising Model", Fig. 3D_snake): an Lx x Ly x Lz cubic grid with open
+ *                       boundaries, one qubit per MPS site (d = 2), sites along a 3D snake (layer
+ *                       z = 0 .. Lz-1; the rows x of a layer run forward in even layers and backward
+ *                       in odd ones; each row y runs forward or backward in turn along the path, so
+ *                       that consecutive sites are lattice neighbours).  Qubit (x, y, z) has the
+ *                       global index (z Lx + x) Ly + y.  2 <= Lx, Ly, Lz <= 16, Lx Ly Lz <= 512. */
+typedef enum { MPSGB_LATTICE_2D_GROUPED = 0, MPSGB_LATTICE_3D_SITES = 1 } mpsgb_lattice;
+
 typedef struct {
-  int Lx, Ly;          /* grid: Lx rows of Ly qubits, periodic in both directions; 2 <= Lx <= 16,
-                          2 <= Ly <= 10 (blocks of at most 2^5 states), Lx * Ly <= 160 */
+  int Lx, Ly;          /* 2D grid: Lx rows of Ly qubits, periodic in both directions; 2 <= Lx <= 16,
+                          2 <= Ly <= 10 (blocks of at most 2^5 states), Lx * Ly <= 160.
+                          3D grid: see mpsgb_lattice */
   int chi_max;         /* maximum bond dimension chi (>= 1) */
   double theta;        /* absolute initial angle of Eq. initial_state (use mpsgb_initial_theta) */
   mpsgb_precision prec;
@@ -81,6 +96,8 @@ typedef struct {
   unsigned long long seed; /* recorded only: the method draws no random numbers */
   double J, h, dt;     /* evolution parameters used by mpsgb_batch_step */
   int trotter_order;   /* 1: X then ZZ per step; 2: Eq. trotter_step */
+  mpsgb_lattice lattice;
+  int Lz;              /* layers of the 3D lattice (0 or 1 for the 2D lattice) */
 } mpsgb_config;
 
 /* Device allocator used for every allocation of a handle.  alloc returns NULL on failure.
@@ -150,14 +167,18 @@ int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes);
  * at a time): every handle in hs[0 .. count-1] applies nlayers Trotter layers U(dt) (Eq.
  * trotter_step for order 2, X then ZZ for order 1) with the J, h, dt and order of its own config.
  * Handles advance concurrently, one host thread and the handle's own CUDA stream each, so their
- * kernels overlap on the device.  use_graph must be 0: the truncation decisions (kept counts,
- * fidelities) are read back to the host after every eigensolve or SVD, so a layer is not a
- * fixed launch sequence that a CUDA graph could replay; EINVAL otherwise.  The handles must be
- * distinct.  Returns the first failing status (with the handle's index in the message). */
+ * kernels overlap on the device (handles that share a stream, e.g. the legacy default stream,
+ * serialise there).  use_graph = 1: the fixed launch sequences inside a layer (Cholesky
+ * factorisations, eigenvector back-transformations) are recorded once per size and buffer set as
+ * CUDA graphs and replayed, on handles whose stream is not the legacy default stream; use_graph = 0
+ * issues every launch directly.  A whole layer is not one graph: the truncation decisions (kept
+ * counts, fidelities) are read back to the host after every eigensolve or SVD and decide the
+ * shapes of what follows.  The handles must be distinct; use_graph other than 0 or 1 is EINVAL.
+ * Returns the first failing status (with the handle's index in the message). */
 int mpsgb_batch_step(mpsgb_handle* hs, int count, int nlayers, int use_graph);
 
 /* Write / read a checkpoint: config, bond dims, centre, F_MPS, counters and all blocks.  Not from
- * the paper: persistence of this library (file layout: "MPSGBv1\0", the config struct, four ints
+ * the paper: persistence of this library (file layout: "MPSGBv2\0", the config struct, four ints
  * {element bytes, blocks, centre, 0}, F as a double, five 64-bit counters, the bond dims as ints,
  * then every block (left, d, right) row-major complex in the form's element type).
  * mpsgb_load creates a new handle (alloc and stream as in mpsgb_create).  Errors: EINVAL for an
@@ -255,8 +276,21 @@ int mpsgb_schedule_info(int Lx, int Ly, long long out[6]);
  * (p, q, qubit_i, qubit_j, bit_i, bit_j), at most cap gates; *n receives the gate count. */
 int mpsgb_schedule_gates(int Lx, int Ly, int* out, int cap, int* n);
 
-/* Host-only: theta_min + dtheta with theta_min = asin(h / (4 J)) (Sec. II). */
+/* The same two queries for the lattice of a config (cfg->lattice, Lx, Ly, Lz; host only).  For
+ * LATTICE_3D_SITES every site holds one qubit (bit positions 0) and every ZZ bond is an
+ * inter-site gate.  Errors: EINVAL for an unsupported lattice. */
+int mpsgb_config_schedule_info(const mpsgb_config* cfg, long long out[6]);
+int mpsgb_config_schedule_gates(const mpsgb_config* cfg, int* out, int cap, int* n);
+
+/* Host-only: theta_min + dtheta with theta_min = asin(h / (4 J)) (Sec. II; 4 = neighbours of a
+ * site of the square lattice). */
 double mpsgb_initial_theta(double J, double hx, double dtheta);
+
+/* Host-only: theta_min + dtheta for a lattice, theta_min = asin(h / (z J)) with z the number of
+ * neighbours of a site: 4 for LATTICE_2D_GROUPED (Sec. II), 6 for LATTICE_3D_SITES (the 3D
+ * variant starts from the same product state, Eq. initial_state; z = 6 is the cubic lattice's
+ * coordination, the mean-field minimum of the bulk).  NaN for an unknown lattice. */
+double mpsgb_initial_theta_lattice(mpsgb_lattice lattice, double J, double hx, double dtheta);
 
 /* Host-only: gamma_fit = a log2(chi)/n + b of Table gamma_scaling; temperature 0 = low
  * (dtheta = 0), 1 = mid (2 pi/9), 2 = high (3 pi/9).  Returns NaN for another temperature. */

@@ -16,6 +16,11 @@ Readings where the paper is silent:
 """
 from . import model
 
+# 3D variant (Supplemental Material, 3D TFIM section and Fig. 3D_snake): one qubit per MPS site.
+# Reading of the snake where the figure is not reproduced: layer z = 0, 1, ... in turn; in layer z
+# the rows x run 0 .. Lx-1 for even z and Lx-1 .. 0 for odd z; the k-th row visited overall runs
+# y = 0 .. Ly-1 for even k and Ly-1 .. 0 for odd k.  Consecutive sites are then lattice neighbours.
+
 
 def blocks(Lx, Ly):
     """Blocks in MPS order: list of dicts {row, group, qubits (global, big-endian), d}."""
@@ -30,19 +35,33 @@ def blocks(Lx, Ly):
     return out
 
 
-def qubit_home(Lx, Ly):
+def blocks_3d(Lx, Ly, Lz):
+    """Sites of the 3D one-to-one mapping in MPS order: list of dicts {xyz, qubits, d = 2}."""
+    out = []
+    k = 0
+    for z in range(Lz):
+        for i in range(Lx):
+            x = i if z % 2 == 0 else Lx - 1 - i
+            for j in range(Ly):
+                y = j if k % 2 == 0 else Ly - 1 - j
+                out.append({"xyz": (x, y, z), "qubits": [(z * Lx + x) * Ly + y], "d": 2})
+            k += 1
+    return out
+
+
+def qubit_home(Lx, Ly, blks=None):
     """Map global qubit -> (MPS position, bit position from the most significant end)."""
     home = {}
-    for p, b in enumerate(blocks(Lx, Ly)):
+    for p, b in enumerate(blks if blks is not None else blocks(Lx, Ly)):
         for t, q in enumerate(b["qubits"]):
             home[q] = (p, t)
     return home
 
 
-def bond_bounds(Lx, Ly):
+def bond_bounds(Lx, Ly, blks=None):
     """Exact bond dimension bound of bond m (between blocks m and m+1): the smaller of
     the Hilbert-space dimensions on either side."""
-    ds = [b["d"] for b in blocks(Lx, Ly)]
+    ds = [b["d"] for b in (blks if blks is not None else blocks(Lx, Ly))]
     bounds = []
     for m in range(len(ds) - 1):
         left = 1
@@ -63,11 +82,18 @@ def schedule(Lx, Ly):
       inter    = list of (p, q, qi, qj, ti, tj) with p < q the block positions,
                  qi/qj the global qubits and ti/tj their bit positions.
     """
-    home = qubit_home(Lx, Ly)
-    nblk = 2 * Lx
+    return _split_bonds(qubit_home(Lx, Ly), 2 * Lx, model.lattice_bonds(Lx, Ly))
+
+
+def schedule_3d(Lx, Ly, Lz):
+    """(intra, inter) of the 3D one-to-one mapping, as schedule(): every bond is an inter-site gate."""
+    return _split_bonds(qubit_home(0, 0, blocks_3d(Lx, Ly, Lz)), Lx * Ly * Lz, model.lattice_bonds_3d(Lx, Ly, Lz))
+
+
+def _split_bonds(home, nblk, bonds):
     intra = [[] for _ in range(nblk)]
     inter = []
-    for (q1, q2) in model.lattice_bonds(Lx, Ly):
+    for (q1, q2) in bonds:
         p1, t1 = home[q1]
         p2, t2 = home[q2]
         if p1 == p2:

@@ -1,5 +1,10 @@
 """TFIM model definitions (test infrastructure only; see oracle/__init__.py).
 
+Supplemental Material, section "3D Transverse Field Ising Model": the same Hamiltonian on an
+Lx x Ly x Lz cubic grid with open boundaries, the same product initial state, the temperatures
+dtheta = 0, pi/9, 2 pi/9.  Reading where that section is silent: theta_min keeps its definition
+asin(h / (d J)) with d = 6, the number of neighbours of a bulk site of the cubic lattice.
+
 Sec. II, Eq. hamiltonian: H = J sum_<ij> Z_i Z_j + h sum_i X_i, nearest
 neighbours with periodic boundaries on an Lx x Ly square lattice.
 Sec. II, Eq. initial_state: |Psi(theta)> = prod_j (cos(theta/2)|0> + sin(theta/2)|1>).
@@ -23,6 +28,8 @@ DT_PAPER = 0.25
 COORDINATION = 4  # neighbours of a site on the square lattice (the "d" of theta_min)
 
 TEMPERATURES = {"low": 0.0, "mid": 2.0 * math.pi / 9.0, "high": 3.0 * math.pi / 9.0}
+COORDINATION_3D = 6
+TEMPERATURES_3D = {"low": 0.0, "mid": math.pi / 9.0, "high": 2.0 * math.pi / 9.0}
 
 
 def theta_min(J=J_PAPER, h=H_PAPER, coordination=COORDINATION):
@@ -30,9 +37,9 @@ def theta_min(J=J_PAPER, h=H_PAPER, coordination=COORDINATION):
     return math.asin(h / (coordination * J))
 
 
-def initial_theta(dtheta, J=J_PAPER, h=H_PAPER):
+def initial_theta(dtheta, J=J_PAPER, h=H_PAPER, coordination=COORDINATION):
     """Sec. II: theta = theta_min + dtheta."""
-    return theta_min(J, h) + dtheta
+    return theta_min(J, h, coordination) + dtheta
 
 
 def mean_field_energy_per_site(theta, J=J_PAPER, h=H_PAPER, coordination=COORDINATION):
@@ -65,4 +72,20 @@ def lattice_bonds(Lx, Ly):
                 q2 = rr * Ly + cc
                 if q2 != q:
                     bonds.add((min(q, q2), max(q, q2)))
+    return sorted(bonds)
+
+
+def lattice_bonds_3d(Lx, Ly, Lz):
+    """Nearest-neighbour pairs (q1 < q2) of the open Lx x Ly x Lz cubic grid; qubit (x, y, z) has
+    the index (z Lx + x) Ly + y."""
+    def q(x, y, z):
+        return (z * Lx + x) * Ly + y
+
+    bonds = []
+    for z in range(Lz):
+        for x in range(Lx):
+            for y in range(Ly):
+                for (xx, yy, zz) in ((x + 1, y, z), (x, y + 1, z), (x, y, z + 1)):
+                    if xx < Lx and yy < Ly and zz < Lz:
+                        bonds.append((q(x, y, z), q(xx, yy, zz)))
     return sorted(bonds)

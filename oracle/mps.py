@@ -41,11 +41,12 @@ def _rank_keep(s, shape, chi):
 class MPS:
     """Grouped-qubit MPS with an explicit orthogonality centre (a block index)."""
 
-    def __init__(self, Lx, Ly, chi, theta):
-        """theta: the angle of Eq. initial_state, or one angle per qubit (index r * Ly + c)."""
-        self.Lx, self.Ly, self.chi = Lx, Ly, chi
-        self.layout = layout.blocks(Lx, Ly)
-        self.n = Lx * Ly
+    def __init__(self, Lx, Ly, chi, theta, Lz=None):
+        """theta: the angle of Eq. initial_state, or one angle per qubit (global qubit index).
+        Lz: None for the grouped 2D grid; a layer count for the 3D one-to-one mapping."""
+        self.Lx, self.Ly, self.Lz, self.chi = Lx, Ly, Lz, chi
+        self.layout = layout.blocks(Lx, Ly) if Lz is None else layout.blocks_3d(Lx, Ly, Lz)
+        self.n = sum(len(b["qubits"]) for b in self.layout)
         thetas = np.broadcast_to(np.asarray(theta, dtype=np.float64), (self.n,))
         self.blocks = []
         for b in self.layout:
@@ -304,18 +305,18 @@ class MPS:
         return s
 
 
-def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0):
+def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0, Lz=None):
     """Seeded random MPS with every bond at min(chi, bound), in canonical form with the
     orthogonality centre on block `centre`, unit norm.  Entries are complex normal; with `decay`
     every block is scaled by exp(-b / decay) along its right bond index b, so that the Schmidt
     spectra fall off over the bond (a uniformly random state has nearly flat spectra).  The gauge
     moves are this module's QR / LQ steps.  An input generator for generic states: it computes
     nothing of the method and has no pin of its own (its outputs are checked for canonical form
-    and norm where they are used)."""
+    and norm where they are used).  Lz: layer count of the open 3D grid (one qubit per site)."""
     rng = np.random.default_rng(seed)
-    m = MPS(Lx, Ly, chi, 0.3)
+    m = MPS(Lx, Ly, chi, 0.3, Lz=Lz)
     ds = [b["d"] for b in m.layout]
-    bd = [1] + [int(min(chi, b)) for b in layout.bond_bounds(Lx, Ly)] + [1]
+    bd = [1] + [int(min(chi, b)) for b in layout.bond_bounds(Lx, Ly, m.layout)] + [1]
     blocks = []
     for i in range(len(ds)):
         shape = (bd[i], ds[i], bd[i + 1])
@@ -331,16 +332,17 @@ def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0):
     return m
 
 
-def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False, route="mpo"):
+def run(Lx, Ly, chi, theta, J, h, dt, steps, order=2, record_spectra=False, route="mpo", Lz=None):
     """TEBD run of Eq. trotter_step (order 2) or X-then-ZZ (order 1); inter-block gates by the MPO
-    sweep (route "mpo", Sec. III) or by SWAP routing (route "swap").
+    sweep (route "mpo", Sec. III) or by SWAP routing (route "swap").  Lz: None for the grouped 2D
+    grid, else the layer count of the open 3D grid with one qubit per site.
 
     Returns a dict with per-step arrays (entry 0 = initial state): Z, Z2, X, F, plus the
     list of truncation fidelities, final bond dims and the MPS itself.
     """
     alpha, phi = model.layer_angles(J, h, dt, order)
-    intra, inter = layout.schedule(Lx, Ly)
-    psi = MPS(Lx, Ly, chi, theta)
+    intra, inter = layout.schedule(Lx, Ly) if Lz is None else layout.schedule_3d(Lx, Ly, Lz)
+    psi = MPS(Lx, Ly, chi, theta, Lz=Lz)
     rec = {"Z": [], "Z2": [], "X": [], "F": [], "spectra": [], "gap": []}
 
     def record():

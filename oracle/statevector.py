@@ -59,12 +59,13 @@ def x_layer(psi, n, alpha):
     return psi
 
 
-def zz_energy(Lx, Ly):
-    """E(z) = sum_<ij> z_i z_j for every basis state."""
-    n = Lx * Ly
+def zz_energy(Lx, Ly, Lz=None):
+    """E(z) = sum_<ij> z_i z_j for every basis state (periodic 2D grid, or open 3D grid)."""
+    n = Lx * Ly * (Lz or 1)
     z = _z_values(n).astype(np.int32)
     e = np.zeros(2 ** n, dtype=np.int32)
-    for (a, b) in model.lattice_bonds(Lx, Ly):
+    bonds = model.lattice_bonds(Lx, Ly) if Lz is None else model.lattice_bonds_3d(Lx, Ly, Lz)
+    for (a, b) in bonds:
         e += z[a] * z[b]
     return e
 
@@ -88,11 +89,11 @@ def observables(psi, n):
     return ztot, z2, float(xs / (n * norm)), float(norm)
 
 
-def run(Lx, Ly, theta, J, h, dt, steps, order=2):
+def run(Lx, Ly, theta, J, h, dt, steps, order=2, Lz=None):
     """Trotter evolution; returns per-step arrays (step 0 = initial state) and psi."""
-    n = Lx * Ly
+    n = Lx * Ly * (Lz or 1)
     alpha, phi = model.layer_angles(J, h, dt, order)
-    energy = zz_energy(Lx, Ly)
+    energy = zz_energy(Lx, Ly, Lz)
     psi = product_state(n, theta)
     rec = {"Z": [], "Z2": [], "X": []}
 

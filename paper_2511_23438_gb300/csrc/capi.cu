@@ -50,7 +50,7 @@ int check_config(const mpsgb_config* c) {
   if (c->chi_max < 1 || c->chi_max > 8192) return fail(MPSGB_EINVAL, "chi_max must be in 1..8192");
   mpsgb::Layout L;
   std::string err;
-  if (!mpsgb::make_layout(c->Lx, c->Ly, L, err)) return fail(MPSGB_EINVAL, err);
+  if (!mpsgb::make_layout(*c, L, err)) return fail(MPSGB_EINVAL, err);
   return MPSGB_OK;
 }
 
@@ -66,6 +66,26 @@ int create_impl(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* str
   auto* h = new mpsgb_mps();
   h->e = e;
   *out = h;
+  return MPSGB_OK;
+}
+int schedule_info_of(const mpsgb::Layout& L, long long out[6]) {
+  long long nintra = 0, ntr = 0;
+  int dmax = 1;
+  for (auto& v : L.intra) nintra += (long long)v.size();
+  for (auto& g : L.inter) ntr += g.q - g.p;
+  for (int k : L.k) dmax = std::max(dmax, 1 << k);
+  out[0] = L.N; out[1] = nintra + (long long)L.inter.size(); out[2] = nintra;
+  out[3] = (long long)L.inter.size(); out[4] = ntr; out[5] = dmax;
+  return MPSGB_OK;
+}
+
+int schedule_gates_of(const mpsgb::Layout& L, int* out, int cap, int* n) {
+  *n = (int)L.inter.size();
+  for (int i = 0; i < cap && i < (int)L.inter.size(); ++i) {
+    const auto& g = L.inter[i];
+    int v[6] = {g.p, g.q, g.qi, g.qj, g.ti, g.tj};
+    for (int j = 0; j < 6; ++j) out[6 * i + j] = v[j];
+  }
   return MPSGB_OK;
 }
 }  // namespace
@@ -149,7 +169,7 @@ int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes) {
   if (s) return s;
   mpsgb::Layout L;
   std::string err;
-  mpsgb::make_layout(cfg->Lx, cfg->Ly, L, err);
+  if (!mpsgb::make_layout(*cfg, L, err)) return fail(MPSGB_EINVAL, err);
   double mb = 1;
   for (double b : L.bound) mb = std::max(mb, b);
   double chi = std::min<double>(cfg->chi_max, mb);
@@ -162,8 +182,7 @@ int mpsgb_footprint_bytes(const mpsgb_config* cfg, size_t* bytes) {
 
 int mpsgb_batch_step(mpsgb_handle* hs, int count, int nlayers, int use_graph) {
   if (!hs || count < 0 || nlayers < 0) return fail(MPSGB_EINVAL, "bad batch arguments");
-  if (use_graph != 0)
-    return fail(MPSGB_EINVAL, "use_graph: truncation decisions are read back on the host, no CUDA graph replay");
+  if (use_graph != 0 && use_graph != 1) return fail(MPSGB_EINVAL, "use_graph must be 0 or 1");
   const int nsteps = nlayers;
   for (int i = 0; i < count; ++i) {
     if (!hs[i] || !hs[i]->e) return fail(MPSGB_EINVAL, "null handle in batch");
@@ -176,6 +195,7 @@ int mpsgb_batch_step(mpsgb_handle* hs, int count, int nlayers, int use_graph) {
   th.reserve(count);
   for (int i = 0; i < count; ++i)
     th.emplace_back([&, i] {
+      mpsgb::set_graphs_enabled(use_graph != 0);
       const mpsgb_config& c = hs[i]->e->cfg;
       st[i] = mpsgb_step(hs[i], c.J, c.h, c.dt, c.trotter_order, nsteps);
       if (st[i]) msg[i] = mpsgb_last_error();
@@ -200,7 +220,7 @@ int mpsgb_load(const char* path, const mpsgb_allocator* alloc, void* cuda_stream
     if (!fh) return fail(MPSGB_EINVAL, std::string("cannot open ") + path);
     char magic[8];
     mpsgb_config cfg;
-    if (std::fread(magic, 1, 8, fh) != 8 || std::memcmp(magic, "MPSGBv1", 8) != 0 ||
+    if (std::fread(magic, 1, 8, fh) != 8 || std::memcmp(magic, "MPSGBv2", 8) != 0 ||
         std::fread(&cfg, sizeof(cfg), 1, fh) != 1) {
       std::fclose(fh);
       return fail(MPSGB_EINVAL, "not an mpsgb checkpoint");
@@ -258,14 +278,7 @@ int mpsgb_schedule_info(int Lx, int Ly, long long out[6]) {
   mpsgb::Layout L;
   std::string err;
   if (!mpsgb::make_layout(Lx, Ly, L, err)) return fail(MPSGB_EINVAL, err);
-  long long nintra = 0, ntr = 0;
-  int dmax = 1;
-  for (auto& v : L.intra) nintra += (long long)v.size();
-  for (auto& g : L.inter) ntr += g.q - g.p;
-  for (int k : L.k) dmax = std::max(dmax, 1 << k);
-  out[0] = L.N; out[1] = nintra + (long long)L.inter.size(); out[2] = nintra;
-  out[3] = (long long)L.inter.size(); out[4] = ntr; out[5] = dmax;
-  return MPSGB_OK;
+  return schedule_info_of(L, out);
 }
 
 int mpsgb_schedule_gates(int Lx, int Ly, int* out, int cap, int* n) {
@@ -273,13 +286,23 @@ int mpsgb_schedule_gates(int Lx, int Ly, int* out, int cap, int* n) {
   mpsgb::Layout L;
   std::string err;
   if (!mpsgb::make_layout(Lx, Ly, L, err)) return fail(MPSGB_EINVAL, err);
-  *n = (int)L.inter.size();
-  for (int i = 0; i < cap && i < (int)L.inter.size(); ++i) {
-    const auto& g = L.inter[i];
-    int v[6] = {g.p, g.q, g.qi, g.qj, g.ti, g.tj};
-    for (int j = 0; j < 6; ++j) out[6 * i + j] = v[j];
-  }
-  return MPSGB_OK;
+  return schedule_gates_of(L, out, cap, n);
+}
+
+int mpsgb_config_schedule_info(const mpsgb_config* cfg, long long out[6]) {
+  if (!cfg || !out) return fail(MPSGB_EINVAL, "null argument");
+  mpsgb::Layout L;
+  std::string err;
+  if (!mpsgb::make_layout(*cfg, L, err)) return fail(MPSGB_EINVAL, err);
+  return schedule_info_of(L, out);
+}
+
+int mpsgb_config_schedule_gates(const mpsgb_config* cfg, int* out, int cap, int* n) {
+  if (!cfg || !n || (cap > 0 && !out)) return fail(MPSGB_EINVAL, "null argument");
+  mpsgb::Layout L;
+  std::string err;
+  if (!mpsgb::make_layout(*cfg, L, err)) return fail(MPSGB_EINVAL, err);
+  return schedule_gates_of(L, out, cap, n);
 }
 
 int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err) {
@@ -321,6 +344,12 @@ int mpsgb_eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, v
 }
 
 double mpsgb_initial_theta(double J, double hx, double dtheta) { return std::asin(hx / (4.0 * J)) + dtheta; }
+
+double mpsgb_initial_theta_lattice(mpsgb_lattice lattice, double J, double hx, double dtheta) {
+  const double z = lattice == MPSGB_LATTICE_2D_GROUPED ? 4.0 : lattice == MPSGB_LATTICE_3D_SITES ? 6.0 : 0.0;
+  if (z == 0.0) return std::nan("");
+  return std::asin(hx / (z * J)) + dtheta;
+}
 
 double mpsgb_gamma_fit(int temperature, int chi, int n) {
   // Table gamma_scaling: (a, b) for low / mid / high

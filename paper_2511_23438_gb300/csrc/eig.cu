@@ -446,14 +446,22 @@ int eigh(cudaStream_t st, int n, const Cx<R>* A, long long lda, long long sA, R*
     count_launch();
   }
   int sweeps = -1;
-  // pinned host copy of the per-problem "rotated" flags, kept per host thread
-  thread_local int* hflag = nullptr;
-  thread_local int hcap = 0;
-  if (hcap < batch) {
-    if (hflag) cudaFreeHost(hflag);
-    hcap = batch < 64 ? 64 : batch;
-    if (cudaMallocHost(&hflag, sizeof(int) * hcap) != cudaSuccess) { hflag = nullptr; hcap = 0; return -1; }
+  // pinned host copy of the per-problem "rotated" flags, kept per host thread and released when
+  // the thread ends
+  struct PinnedFlags {
+    int* p = nullptr;
+    int cap = 0;
+    ~PinnedFlags() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  thread_local PinnedFlags pf;
+  if (pf.cap < batch) {
+    if (pf.p) cudaFreeHost(pf.p);
+    pf.cap = batch < 64 ? 64 : batch;
+    if (cudaMallocHost(&pf.p, sizeof(int) * pf.cap) != cudaSuccess) { pf.p = nullptr; pf.cap = 0; return -1; }
   }
+  int* hflag = pf.p;
   const int max_sweeps = 40;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     cudaMemsetAsync(flag, 0, sizeof(int) * batch, st);

@@ -41,6 +41,26 @@
 namespace mpsgb {
 
 // ------------------------------------------------------------------ layout
+namespace {
+// gate order (first block, second block, first qubit, second qubit) and the exact bond bounds
+void finish_layout(Layout& L) {
+  std::sort(L.inter.begin(), L.inter.end(), [](const Layout::Gate& a, const Layout::Gate& b) {
+    if (a.p != b.p) return a.p < b.p;
+    if (a.q != b.q) return a.q < b.q;
+    if (a.qi != b.qi) return a.qi < b.qi;
+    return a.qj < b.qj;
+  });
+  L.bound.assign(L.N - 1, 0);
+  int total = 0;
+  for (int b = 0; b < L.N; ++b) total += L.k[b];
+  int left = 0;
+  for (int m = 0; m < L.N - 1; ++m) {
+    left += L.k[m];
+    L.bound[m] = std::ldexp(1.0, std::min(left, total - left));
+  }
+}
+}  // namespace
+
 bool make_layout(int Lx, int Ly, Layout& L, std::string& err) {
   if (Lx < 2 || Ly < 2 || Lx > 16 || Ly > 10 || Lx * Ly > 160) {
     err = "grid must have 2 <= Lx <= 16, 2 <= Ly <= 10 and at most 160 qubits";
@@ -82,21 +102,61 @@ bool make_layout(int Lx, int Ly, Layout& L, std::string& err) {
       L.inter.push_back(g);
     }
   }
-  std::sort(L.inter.begin(), L.inter.end(), [](const Layout::Gate& a, const Layout::Gate& b) {
-    if (a.p != b.p) return a.p < b.p;
-    if (a.q != b.q) return a.q < b.q;
-    if (a.qi != b.qi) return a.qi < b.qi;
-    return a.qj < b.qj;
-  });
-  L.bound.assign(L.N - 1, 0);
-  int total = 0;
-  for (int b = 0; b < L.N; ++b) total += L.k[b];
-  int left = 0;
-  for (int m = 0; m < L.N - 1; ++m) {
-    left += L.k[m];
-    L.bound[m] = std::ldexp(1.0, std::min(left, total - left));
-  }
+  finish_layout(L);
   return true;
+}
+
+// 3D cubic grid with open boundaries, one qubit per site, sites along a snake through the layers
+bool make_layout_3d(int Lx, int Ly, int Lz, Layout& L, std::string& err) {
+  if (Lx < 2 || Ly < 2 || Lz < 2 || Lx > 16 || Ly > 16 || Lz > 16 || Lx * Ly * Lz > 512) {
+    err = "3D grid must have 2 <= Lx, Ly, Lz <= 16 and at most 512 qubits";
+    return false;
+  }
+  L = Layout();
+  L.Lx = Lx; L.Ly = Ly; L.Lz = Lz; L.n = Lx * Ly * Lz; L.N = L.n;
+  L.k.assign(L.N, 1);
+  L.qubits.assign(L.N, {});
+  L.intra.assign(L.N, {});
+  auto qid = [&](int x, int y, int z) { return (z * Lx + x) * Ly + y; };
+  std::vector<int> pos_of(L.n, -1);
+  int pos = 0, row = 0;
+  for (int z = 0; z < Lz; ++z)
+    for (int i = 0; i < Lx; ++i, ++row) {
+      const int x = (z % 2 == 0) ? i : Lx - 1 - i;
+      for (int j = 0; j < Ly; ++j) {
+        const int y = (row % 2 == 0) ? j : Ly - 1 - j;
+        pos_of[qid(x, y, z)] = pos;
+        L.qubits[pos].push_back(qid(x, y, z));
+        ++pos;
+      }
+    }
+  for (int z = 0; z < Lz; ++z)
+    for (int x = 0; x < Lx; ++x)
+      for (int y = 0; y < Ly; ++y) {
+        const int a = qid(x, y, z);
+        const int nb[3] = {x + 1 < Lx ? qid(x + 1, y, z) : -1, y + 1 < Ly ? qid(x, y + 1, z) : -1,
+                           z + 1 < Lz ? qid(x, y, z + 1) : -1};
+        for (int b : nb) {
+          if (b < 0) continue;
+          const int pa = pos_of[a], pb = pos_of[b];
+          L.inter.push_back(pa < pb ? Layout::Gate{pa, pb, a, b, 0, 0} : Layout::Gate{pb, pa, b, a, 0, 0});
+        }
+      }
+  finish_layout(L);
+  return true;
+}
+
+bool make_layout(const mpsgb_config& c, Layout& L, std::string& err) {
+  if (c.lattice == MPSGB_LATTICE_2D_GROUPED) {
+    if (c.Lz != 0 && c.Lz != 1) {
+      err = "the 2D lattice takes Lz = 0 or 1";
+      return false;
+    }
+    return make_layout(c.Lx, c.Ly, L, err);
+  }
+  if (c.lattice == MPSGB_LATTICE_3D_SITES) return make_layout_3d(c.Lx, c.Ly, c.Lz, L, err);
+  err = "unknown lattice";
+  return false;
 }
 
 // ------------------------------------------------------------------ device memory
@@ -205,7 +265,7 @@ class EngineT : public Engine {
     mem.st = st;
     if (alloc && alloc->alloc && alloc->free) { mem.a = *alloc; mem.custom = true; }
     std::string err;
-    if (!make_layout(c.Lx, c.Ly, L, err)) throw Fail{MPSGB_EINVAL, err};
+    if (!make_layout(c, L, err)) throw Fail{MPSGB_EINVAL, err};
     if (c.chi_max < 1) throw Fail{MPSGB_EINVAL, "chi_max must be >= 1"};
     kpos = L.k;
     swap_route = c.route == MPSGB_ROUTE_SWAP;
@@ -1028,7 +1088,7 @@ class EngineT : public Engine {
   int save(const char* path) override {
     FILE* fh = std::fopen(path, "wb");
     if (!fh) throw Fail{MPSGB_EINVAL, std::string("cannot open ") + path};
-    const char magic[8] = {'M', 'P', 'S', 'G', 'B', 'v', '1', 0};
+    const char magic[8] = {'M', 'P', 'S', 'G', 'B', 'v', '2', 0};
     int hdr[4] = {(int)sizeof(R), L.N, centre, 0};
     long long st5[5] = {stats.truncations, stats.gates, stats.centre_moves, stats.eig_calls, stats.eig_sweeps};
     bool ok = std::fwrite(magic, 1, 8, fh) == 8 && std::fwrite(&cfg, sizeof(cfg), 1, fh) == 1 &&

@@ -16,10 +16,12 @@ struct Fail {
   std::string msg;
 };
 
-// Row-grouped snake layout of an Lx x Ly periodic grid (Sec. III, Fig. mps_drawing).
+// MPS layout of a lattice: row-grouped snake of an Lx x Ly periodic grid (Sec. III, Fig.
+// mps_drawing), or one qubit per site along the 3D snake of an open Lx x Ly x Lz grid (the
+// Supplemental Material's 3D TFIM section, Fig. 3D_snake).
 struct Layout {
   struct Gate { int p, q, qi, qj, ti, tj; };  // block positions p < q, global qubits, bit positions (0 = MSB)
-  int Lx = 0, Ly = 0, N = 0, n = 0;
+  int Lx = 0, Ly = 0, Lz = 1, N = 0, n = 0;
   std::vector<int> k;                                  // qubits per block
   std::vector<std::vector<int>> qubits;                // global qubit ids per block, MSB first
   std::vector<std::vector<std::pair<int, int>>> intra; // in-block ZZ pairs (bit positions)
@@ -27,6 +29,7 @@ struct Layout {
   std::vector<double> bound;                           // exact bond-dimension bound per bond
 };
 bool make_layout(int Lx, int Ly, Layout& out, std::string& err);
+bool make_layout(const mpsgb_config& cfg, Layout& out, std::string& err);
 
 struct Stats {
   long long truncations = 0;     // bond truncations (one per spanned bond of an inter-block gate)

@@ -4,11 +4,15 @@
 // given buffers (the Cholesky recursion, the eigensolver's orthonormalisation and back-
 // transformation), most of them small.  On a capturable stream such a sequence is recorded once
 // per key as a CUDA graph and replayed afterwards, which takes the host launch cost and most gaps
-// off the device timeline.  Graphs are kept per host thread (each handle's work runs on one host
-// thread at a time), at most 64, the oldest dropped first.  The legacy default stream cannot be
-// captured and a stream that is already capturing is not nested into: both run the sequence
-// directly, as does everything while per-launch-site timing is on (so that each kernel stays
-// bracketed by its own events).
+// off the device timeline.  One cache serves the process (at most 512 graphs, the least recently
+// used dropped first); a key holds the stream and every buffer address, and one handle's work runs
+// on one host thread at a time, so no graph is launched from two threads at once.  The legacy
+// default stream cannot be captured and a stream that is already capturing is not nested into:
+// both run the sequence directly, as does everything while per-launch-site timing is on (so that
+// each kernel stays bracketed by its own events) or while the calling thread has graphs switched
+// off (set_graphs_enabled).
+#include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -21,30 +25,62 @@ struct Entry {
   GraphKey key;
   cudaGraphExec_t exec;
   unsigned long long kernels;
+  unsigned long long used;
+  cudaEvent_t done;  // recorded after every launch: an evicted graph is destroyed once it is idle
 };
 struct Cache {
+  std::mutex mu;
   std::vector<Entry> v;
-  ~Cache() {
-    for (auto& e : v) cudaGraphExecDestroy(e.exec);
-  }
+  unsigned long long clock = 0;
 };
-thread_local Cache t_cache;
+void release_all();
+Cache& cache() {
+  // never destroyed: the graphs are released by an exit handler registered after the CUDA runtime
+  // initialised (so it runs before the runtime's own teardown)
+  static Cache* c = [] {
+    Cache* p = new Cache();
+    std::atexit(release_all);
+    return p;
+  }();
+  return *c;
+}
+void release_all() {
+  Cache& c = cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  for (auto& e : c.v) {
+    cudaEventSynchronize(e.done);
+    cudaGraphExecDestroy(e.exec);
+    cudaEventDestroy(e.done);
+  }
+  c.v.clear();
+}
+constexpr size_t kMaxGraphs = 512;
+thread_local bool t_graphs = true;
 }  // namespace
+
+void set_graphs_enabled(bool on) { t_graphs = on; }
+bool graphs_enabled() { return t_graphs; }
 
 int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int()>& issue) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread && !g_kt_enabled &&
-                          cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+  const bool capturable = t_graphs && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread &&
+                          !g_kt_enabled && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
   if (!capturable) {
     if (issue() != 0) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
   }
-  for (auto& e : t_cache.v)
-    if (e.key == key) {
-      if (cudaGraphLaunch(e.exec, st) != cudaSuccess) return -4;
-      count_launch(e.kernels);
-      return 0;
-    }
+  Cache& c = cache();
+  {
+    // launch under the lock, so that no other thread evicts the graph in between
+    std::lock_guard<std::mutex> lk(c.mu);
+    for (auto& e : c.v)
+      if (e.key == key) {
+        e.used = ++c.clock;
+        if (cudaGraphLaunch(e.exec, st) != cudaSuccess || cudaEventRecord(e.done, st) != cudaSuccess) return -4;
+        count_launch(e.kernels);
+        return 0;
+      }
+  }
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -4;
   unsigned long long kernels = 0;  // the captured kernels run (and are counted) at each graph launch
   t_launch_sink = &kernels;
@@ -61,12 +97,38 @@ int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<in
   const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (ei != cudaSuccess || !exec) return -4;
-  if (t_cache.v.size() >= 64) {
-    cudaGraphExecDestroy(t_cache.v.front().exec);
-    t_cache.v.erase(t_cache.v.begin());
+  cudaEvent_t done = nullptr;
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGraphExecDestroy(exec);
+    return -4;
   }
-  t_cache.v.push_back(Entry{key, exec, kernels});
-  if (cudaGraphLaunch(exec, st) != cudaSuccess) return -4;
+  if (cudaGraphLaunch(exec, st) != cudaSuccess || cudaEventRecord(done, st) != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    cudaEventDestroy(done);
+    return -4;
+  }
+  bool evicted = false;
+  Entry drop{};
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (c.v.size() >= kMaxGraphs) {
+      size_t old = 0;
+      for (size_t i = 1; i < c.v.size(); ++i)
+        if (c.v[i].used < c.v[old].used) old = i;
+      drop = c.v[old];
+      evicted = true;
+      c.v.erase(c.v.begin() + old);
+    }
+    c.v.push_back(Entry{key, exec, kernels, ++c.clock, done});
+  }
+  // the evicted graph (of another size, or of another handle) is no longer reachable from the
+  // cache; its last launch is waited for before its resources are released
+  if (evicted) {
+    cudaEventSynchronize(drop.done);
+    cudaGraphExecDestroy(drop.exec);
+    cudaEventDestroy(drop.done);
+  }
   count_launch(kernels);
   return 0;
 }

@@ -20,6 +20,9 @@ struct GraphKey {
 // capturable stream it is recorded once per key as a CUDA graph and replayed; otherwise issued
 // directly.  Returns 0, or -4 if a call or the capture failed.
 int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int()>& issue);
+// graph replay for the calling host thread (on by default)
+void set_graphs_enabled(bool on);
+bool graphs_enabled();
 
 // ---------------------------------------------------------------- GEMM (gemm.cu)
 template <typename R>

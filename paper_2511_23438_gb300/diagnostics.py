@@ -18,7 +18,7 @@ import struct
 
 import numpy as np
 
-MAGIC = b"MPSGBv1\x00"
+MAGIC = b"MPSGBv2\x00"
 
 
 def block_qubits(Lx, Ly):
@@ -57,9 +57,11 @@ def read_checkpoint(path, config_size=None):
     if Config is not None:
         cfg = Config.from_buffer_copy(cfg_raw)
         Lx, Ly = cfg.Lx, cfg.Ly
-    else:  # Lx, Ly are the first two ints of the config
+        three_d = cfg.lattice == 1
+    else:  # Lx, Ly are the first two ints of the config (2D lattice)
         Lx, Ly = struct.unpack_from("2i", cfg_raw, 0)
-    ks = block_qubits(Lx, Ly)
+        three_d = False
+    ks = [1] * (Lx * Ly * cfg.Lz) if three_d else block_qubits(Lx, Ly)
     if len(ks) != nblk:
         raise ValueError("block count does not match the grid")
     dt = np.complex128 if rbytes == 8 else np.complex64

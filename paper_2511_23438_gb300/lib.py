@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmpsgb.so")
 FP64, SPLIT_TF32X3, SPLIT_BF16X3, FP32 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "split_tf32x3": SPLIT_TF32X3, "split_bf16x3": SPLIT_BF16X3, "fp32": FP32}
 ROUTE_MPO, ROUTE_SWAP = 0, 1
+LATTICE_2D_GROUPED, LATTICE_3D_SITES = 0, 1
 LAYER_X, LAYER_ZZ = 0, 1
 Z_TOT, Z_TOT2, X_TOT = 0, 1, 2
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEDOUT", -4: "EDEVICE", -5: "ESTATE"}
@@ -28,7 +29,7 @@ class Config(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("chi_max", ctypes.c_int), ("theta", ctypes.c_double),
                 ("prec", ctypes.c_int), ("route", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("J", ctypes.c_double), ("h", ctypes.c_double), ("dt", ctypes.c_double),
-                ("trotter_order", ctypes.c_int)]
+                ("trotter_order", ctypes.c_int), ("lattice", ctypes.c_int), ("Lz", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -84,6 +85,10 @@ _SIGS = {
     "mpsgb_eigh_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     "mpsgb_initial_theta": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "mpsgb_initial_theta_lattice": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "mpsgb_config_schedule_info": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_longlong)]),
+    "mpsgb_config_schedule_gates": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_int)]),
     "mpsgb_gamma_fit": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mpsgb_rescale": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_double)]),
@@ -117,8 +122,10 @@ def _check(status):
         raise MpsgbError(status, load().mpsgb_last_error().decode())
 
 
-def config(Lx, Ly, chi, theta, prec="fp64", J=-1.0, h=2.0, dt=0.25, order=2, seed=0, route=ROUTE_MPO):
-    return Config(Lx, Ly, chi, theta, PRECISIONS[prec] if isinstance(prec, str) else prec, route, seed, J, h, dt, order)
+def config(Lx, Ly, chi, theta, prec="fp64", J=-1.0, h=2.0, dt=0.25, order=2, seed=0, route=ROUTE_MPO,
+           lattice=LATTICE_2D_GROUPED, Lz=1):
+    return Config(Lx, Ly, chi, theta, PRECISIONS[prec] if isinstance(prec, str) else prec, route, seed, J, h, dt, order,
+                  lattice, Lz)
 
 
 def convert_checkpoint(src, dst, prec):
@@ -130,7 +137,7 @@ def convert_checkpoint(src, dst, prec):
     with open(src, "rb") as fh:
         raw = fh.read()
     n_cfg = ctypes.sizeof(Config)
-    if raw[:8] != b"MPSGBv1\0":
+    if raw[:8] != b"MPSGBv2\0":
         raise ValueError("not an mpsgb checkpoint: %s" % src)
     cfg = Config.from_buffer_copy(raw[8:8 + n_cfg])
     off = 8 + n_cfg
@@ -144,7 +151,7 @@ def convert_checkpoint(src, dst, prec):
     cfg.prec = PRECISIONS[prec] if isinstance(prec, str) else prec
     out_t = np.complex128 if cfg.prec == FP64 else np.complex64
     with open(dst, "wb") as fh:
-        fh.write(b"MPSGBv1\0")
+        fh.write(b"MPSGBv2\0")
         fh.write(bytes(cfg))
         fh.write(struct.pack("4i", 8 if out_t == np.complex128 else 4, nblk, centre, zero))
         fh.write(head)
@@ -207,8 +214,10 @@ def set_wait_limit(cycles):
     return load().mpsgb_set_wait_limit(int(cycles))
 
 
-def initial_theta(J, h, dtheta):
-    return load().mpsgb_initial_theta(J, h, dtheta)
+def initial_theta(J, h, dtheta, lattice=None):
+    if lattice is None:
+        return load().mpsgb_initial_theta(J, h, dtheta)
+    return load().mpsgb_initial_theta_lattice(lattice, J, h, dtheta)
 
 
 def gamma_fit(temperature, chi, n):
@@ -221,18 +230,29 @@ def rescale(z, z2, F, gamma):
     return out[0], out[1]
 
 
-def schedule_info(Lx, Ly):
+def schedule_info(Lx, Ly=None):
+    """Schedule facts of an Lx x Ly grid, or of the lattice of a Config passed as the first argument."""
     out = (ctypes.c_longlong * 6)()
-    _check(load().mpsgb_schedule_info(Lx, Ly, out))
+    if isinstance(Lx, Config):
+        _check(load().mpsgb_config_schedule_info(ctypes.byref(Lx), out))
+    else:
+        _check(load().mpsgb_schedule_info(Lx, Ly, out))
     keys = ("blocks", "zz_bonds", "intra", "inter", "truncations", "dmax")
     return dict(zip(keys, list(out)))
 
 
-def schedule_gates(Lx, Ly):
+def schedule_gates(Lx, Ly=None):
+    """Inter-block gates in application order, of an Lx x Ly grid or of a Config's lattice."""
     n = ctypes.c_int()
-    _check(load().mpsgb_schedule_gates(Lx, Ly, None, 0, ctypes.byref(n)))
+    if isinstance(Lx, Config):
+        def query(buf, cap):
+            _check(load().mpsgb_config_schedule_gates(ctypes.byref(Lx), buf, cap, ctypes.byref(n)))
+    else:
+        def query(buf, cap):
+            _check(load().mpsgb_schedule_gates(Lx, Ly, buf, cap, ctypes.byref(n)))
+    query(None, 0)
     buf = (ctypes.c_int * (6 * n.value))()
-    _check(load().mpsgb_schedule_gates(Lx, Ly, buf, n.value, ctypes.byref(n)))
+    query(buf, n.value)
     v = list(buf)
     return [tuple(v[6 * i: 6 * i + 6]) for i in range(n.value)]
 
@@ -355,7 +375,7 @@ class MPS:
         _check(load().mpsgb_save(self.h, path.encode()))
 
 
-def batch_step(mps_list, nlayers, use_graph=0):
+def batch_step(mps_list, nlayers, use_graph=1):
     arr = (ctypes.c_void_p * len(mps_list))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
                                               for m in mps_list])
     _check(load().mpsgb_batch_step(arr, len(mps_list), nlayers, use_graph))

@@ -104,7 +104,7 @@ def _write_checkpoint(L, path, cfg, m, dtype=np.complex128):
     # layout of mpsgb_save: magic, config, {real bytes, blocks, centre, 0}, F, 5 counters,
     # bond dims, then every block (left, d, right) row-major complex128 (FP64 form) or complex64
     with open(path, "wb") as fh:
-        fh.write(b"MPSGBv1\0")
+        fh.write(b"MPSGBv2\0")
         fh.write(bytes(cfg))
         fh.write(struct.pack("4i", 8 if dtype == np.complex128 else 4, len(m.blocks), m.centre, 0))
         fh.write(struct.pack("d", 1.0))

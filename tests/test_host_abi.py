@@ -51,8 +51,31 @@ def test_schedule_matches_oracle(lib, grid):
     assert lib.schedule_gates(*grid) == [tuple(g) for g in inter]
 
 
+@pytest.mark.parametrize("dims", [(2, 2, 2), (2, 3, 4), (3, 3, 4), (4, 4, 4), (3, 4, 2)])
+def test_3d_schedule_matches_oracle(lib, dims):
+    # open cubic grid, one qubit per site along the 3D snake: the library's gate list (positions,
+    # qubits, bit positions) equals the oracle's, element by element
+    Lx, Ly, Lz = dims
+    cfg = lib.config(Lx, Ly, 16, 0.1, lattice=lib.LATTICE_3D_SITES, Lz=Lz)
+    _, inter = layout.schedule_3d(Lx, Ly, Lz)
+    assert lib.schedule_gates(cfg) == [tuple(g) for g in inter]
+    info = lib.schedule_info(cfg)
+    assert info["blocks"] == Lx * Ly * Lz and info["intra"] == 0 and info["dmax"] == 2
+    assert info["inter"] == len(inter) and info["truncations"] == sum(g[1] - g[0] for g in inter)
+    # 2D configs give the same answers through either query
+    c2 = lib.config(5, 6, 16, 0.1)
+    assert lib.schedule_gates(c2) == lib.schedule_gates(5, 6)
+    # footprint: chi capped by the largest exact bound (2^(n/2)), d = 2, one site per qubit
+    chi = min(16, 2 ** (Lx * Ly * Lz // 2))
+    assert lib.footprint_bytes(cfg) == chi * chi * 2 * Lx * Ly * Lz * 16
+
+
 def test_host_formulas(lib):
     assert abs(lib.initial_theta(-1.0, 2.0, 0.0) - model.theta_min()) < 1e-15
+    assert abs(lib.initial_theta(-1.0, 2.0, 0.0, lattice=lib.LATTICE_2D_GROUPED) - model.theta_min()) < 1e-15
+    t3 = model.initial_theta(math.pi / 9, coordination=model.COORDINATION_3D)
+    assert abs(lib.initial_theta(-1.0, 2.0, math.pi / 9, lattice=lib.LATTICE_3D_SITES) - t3) < 1e-15
+    assert math.isnan(lib.initial_theta(-1.0, 2.0, 0.0, lattice=5))
     for t, name in enumerate(("low", "mid", "high")):
         for chi, n in [(64, 30), (1024, 48), (4096, 56)]:
             assert abs(lib.gamma_fit(t, chi, n) - rescale.gamma_fit(name, chi, n)) < 1e-15
@@ -72,7 +95,9 @@ def test_footprint(lib):
 
 def test_invalid_arguments_rejected_on_host(lib):
     for cfg in [lib.config(1, 4, 16, 0.1), lib.config(3, 4, 0, 0.1), lib.config(3, 4, 16, float("nan")),
-                lib.config(3, 4, 16, 0.1, prec=7), lib.config(3, 40, 16, 0.1)]:
+                lib.config(3, 4, 16, 0.1, prec=7), lib.config(3, 40, 16, 0.1),
+                lib.config(3, 4, 16, 0.1, Lz=2), lib.config(3, 4, 16, 0.1, lattice=2),
+                lib.config(3, 3, 16, 0.1, lattice=1, Lz=1), lib.config(9, 9, 16, 0.1, lattice=1, Lz=9)]:
         with pytest.raises(lib.MpsgbError) as e:
             lib.MPS(cfg)
         assert e.value.status == -1
