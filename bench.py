@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--batch-mps", type=int, default=32, help="MPS of the batched-advance leg (0: none)")
     ap.add_argument("--three-d", default="3x3x4", help="open 3D grid of the one-qubit-per-site leg ('' : none)")
     ap.add_argument("--three-d-chi", type=int, default=128)
+    ap.add_argument("--xy", default="6x6", help="open grid of the XY-model leg ('' : none)")
+    ap.add_argument("--xy-chi", type=int, default=256)
     ap.add_argument("--peaks", action="store_true", help="measure dense matmul rates (torch) and exit")
     ap.add_argument("--split-error", default="", help="error table of the complex64 forms against the FP64 GPU "
                     "form: comma-separated chi:steps pairs on the 5x6 grid (e.g. 64:20,256:8), then exit")
@@ -266,6 +268,37 @@ def three_d_run(lib, dims, chi, prec, grow=2):
                        "(dtheta=pi/9), %d untimed steps then one timed" % (Lx, Ly, Lz, Lx * Ly * Lz, chi, grow),
            "precision": prec, "bond_updates_per_s": u / (ms / 1e3), "ms_per_step": ms, "bond_updates_per_step": u,
            "F": m.fidelity(), "max_bond": max(m.bond_dims())}
+    m.close()
+    return out
+
+
+def xy_run(lib, dims, chi, prec, grow=1):
+    """The XY workload: open Lx x Ly grid, one qubit per site, g = 1, the initial state of Eq.
+    xy_init at g tau = 0.06 pi (three Trotter steps of g dtau = 0.02 pi, then the staggered Z
+    phases pi/8), quench steps of g dt = 0.05 pi (every gate by SWAP routing); `grow` untimed
+    steps, then one step timed with CUDA events on the handle's stream."""
+    import torch
+    Lx, Ly = (int(v) for v in dims.split("x"))
+    g, dt, dtau = 1.0, 0.05 * math.pi, 0.02 * math.pi
+    s = torch.cuda.Stream()
+    m = lib.MPS(lib.xy_config(Lx, Ly, chi, g, dt, prec=prec), stream=s.cuda_stream)
+    m.step(g, 0.0, dtau, 2, 3)
+    m.apply_layer(lib.LAYER_ZSTAG, math.pi / 8)
+    m.step(g, 0.0, dt, 2, grow)
+    u0 = m.stats()["truncations"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    m.step(g, 0.0, dt, 2, 1)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    u = m.stats()["truncations"] - u0
+    out = {"workload": "XY model %dx%d open grid, one qubit per site, chi=%d, g tau=0.06 pi, g dt=0.05 pi, SWAP "
+                       "routing, %d untimed quench step(s) then one timed" % (Lx, Ly, chi, grow),
+           "precision": prec, "two_site_updates_per_s": u / (ms / 1e3), "ms_per_step": ms,
+           "two_site_updates_per_step": u, "F": m.fidelity(), "X_stag2": m.expect(lib.X_STAG2),
+           "max_bond": max(m.bond_dims())}
     m.close()
     return out
 
@@ -554,6 +587,8 @@ def main():
         line["batched"] = batched_run(lib, args.batch_mps, args.prec)
     if args.three_d and world == 1:
         line["three_d"] = three_d_run(lib, args.three_d, args.three_d_chi, args.prec)
+    if args.xy and world == 1:
+        line["xy"] = xy_run(lib, args.xy, args.xy_chi, args.prec)
     if not args.no_cpu_baseline and world == 1:  # the oracle baseline is timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(Lx, Ly, args.chi, args.cpu_updates)
     print(json.dumps(line), flush=True)

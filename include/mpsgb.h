@@ -68,8 +68,12 @@ typedef enum { MPSGB_FP64 = 0, MPSGB_SPLIT_TF32X3 = 1, MPSGB_SPLIT_BF16X3 = 2, M
  * the gate is one two-site update, and the block is moved back; every two-site update is an SVD
  * truncation).  SWAP routing needs chi * d <= 4096 (EINVAL at creation otherwise). */
 typedef enum { MPSGB_ROUTE_MPO = 0, MPSGB_ROUTE_SWAP = 1 } mpsgb_route;
-typedef enum { MPSGB_LAYER_X = 0, MPSGB_LAYER_ZZ = 1 } mpsgb_layer;
-typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2 } mpsgb_obs;
+/* LAYER_ZSTAG: prod_j exp(-i angle s_j Z_j), the staggered field H_Z = sum_j s_j Z_j of Eq. xy_init,
+ * s_j = (-1)^(sum of the qubit's lattice coordinates) (checkerboard). */
+typedef enum { MPSGB_LAYER_X = 0, MPSGB_LAYER_ZZ = 1, MPSGB_LAYER_ZSTAG = 2 } mpsgb_layer;
+/* X_STAG2: <X_stag^2> = (1/n^2) sum_{j,k} s_j s_k <X_j X_k> (Eq. xy_signal, the XY workload's signal,
+ * s_j as for LAYER_ZSTAG); defined on every lattice. */
+typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2, MPSGB_X_STAG2 = 3 } mpsgb_obs;
 
 /* Lattice and its mapping onto MPS sites.
  *   LATTICE_2D_GROUPED  the paper's main setting (Sec. II-III, Fig. mps_drawing): an Lx x Ly grid,
@@ -83,7 +87,25 @@ typedef enum { MPSGB_Z_TOT = 0, MPSGB_Z_TOT2 = 1, MPSGB_X_TOT = 2 } mpsgb_obs;
  *                       in odd ones; each row y runs forward or backward in turn along the path, so
  *                       that consecutive sites are lattice neighbours).  Qubit (x, y, z) has the
  *                       global index (z Lx + x) Ly + y.  2 <= Lx, Ly, Lz <= 16, Lx Ly Lz <= 512. */
-typedef enum { MPSGB_LATTICE_2D_GROUPED = 0, MPSGB_LATTICE_3D_SITES = 1 } mpsgb_lattice;
+/*   LATTICE_2D_SITES    the XY workload's setting (Supplemental Material, section "XY Model"): an
+ *                       Lx x Ly grid with open boundaries, one qubit per MPS site along a row snake
+ *                       (row r runs forward for even r, backward for odd r); qubit (r, c) has index
+ *                       r Ly + c.  2 <= Lx, Ly <= 16, Lx Ly <= 256.  Lz must be 0 or 1. */
+typedef enum { MPSGB_LATTICE_2D_GROUPED = 0, MPSGB_LATTICE_3D_SITES = 1, MPSGB_LATTICE_2D_SITES = 2 } mpsgb_lattice;
+
+/* Hamiltonian.
+ *   MODEL_TFIM  Eq. hamiltonian, H = J sum_<ij> Z_i Z_j + h sum_i X_i, from the product state of Eq.
+ *               initial_state (cfg.theta); any lattice; both routes.
+ *   MODEL_XY    Eq. XY_hamiltonian, H_XY = (g/2) sum_<ij> (X_i X_j + Y_i Y_j) with g = cfg.J (and
+ *               the J argument of mpsgb_step); LATTICE_2D_SITES, ROUTE_SWAP and trotter_order 2 only
+ *               (EINVAL otherwise).  The handle starts in |Neel>, the ground state of H_Z =
+ *               sum_j s_j Z_j (qubit j in |1> where s_j = +1); a step is Eq. xy_trotter_step (the
+ *               depth-7 product over the bond sets A, B: horizontal bonds starting on even / odd
+ *               columns, C, D: vertical bonds starting on even / odd rows), each two-qubit factor
+ *               exp(-i theta (X X + Y Y)) applied by SWAP routing with a two-site update that
+ *               carries the whole 4 x 4 gate.  Eq. xy_init is mpsgb_step(h, g, 0, dtau, 2, m)
+ *               followed by mpsgb_apply_layer(h, MPSGB_LAYER_ZSTAG, pi / 8). */
+typedef enum { MPSGB_MODEL_TFIM = 0, MPSGB_MODEL_XY = 1 } mpsgb_model;
 
 typedef struct {
   int Lx, Ly;          /* 2D grid: Lx rows of Ly qubits, periodic in both directions; 2 <= Lx <= 16,
@@ -97,7 +119,8 @@ typedef struct {
   double J, h, dt;     /* evolution parameters used by mpsgb_batch_step */
   int trotter_order;   /* 1: X then ZZ per step; 2: Eq. trotter_step */
   mpsgb_lattice lattice;
-  int Lz;              /* layers of the 3D lattice (0 or 1 for the 2D lattice) */
+  int Lz;              /* layers of the 3D lattice (0 or 1 for the 2D lattices) */
+  mpsgb_model model;
 } mpsgb_config;
 
 /* Device allocator used for every allocation of a handle.  alloc returns NULL on failure.
@@ -118,7 +141,10 @@ int mpsgb_create(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* cu
  * (no truncation); LAYER_ZZ applies prod_<ij> exp(-i angle Z_i Z_j): in-block pairs as diagonal
  * phases, then every inter-block gate, in the fixed order of the schedule, as a rank-2 MPO
  * followed by truncation of each spanned bond to chi_max; F_MPS is multiplied by each
- * truncation fidelity.  Errors: EINVAL (NaN angle / bad layer), EDEVICE. */
+ * truncation fidelity; LAYER_ZSTAG applies prod_j exp(-i angle s_j Z_j) block by block (no
+ * truncation; the last factor of Eq. xy_init).  On MODEL_XY handles LAYER_X and LAYER_ZZ are
+ * EINVAL (its layers are the bond sets of mpsgb_step).  Errors: EINVAL (NaN angle / bad layer),
+ * EDEVICE. */
 int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle);
 
 /* Apply only the inter-block gates first .. first+count-1 of the ZZ layer's schedule (the order of
@@ -129,7 +155,10 @@ int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle);
 int mpsgb_apply_gates(mpsgb_handle h, int first, int count, double phi);
 
 /* nsteps Trotter steps: order 2 = X(h dt/2) ZZ(J dt) X(h dt/2) (Eq. trotter_step), order 1 =
- * X(h dt) then ZZ(J dt).  Equivalent to the corresponding apply_layer calls. */
+ * X(h dt) then ZZ(J dt).  Equivalent to the corresponding apply_layer calls.  MODEL_XY: nsteps
+ * applications of Eq. xy_trotter_step with g = J (hx unused, order must be 2); a set of duration s
+ * applies exp(-i (g s / 2)(X X + Y Y)) to each of its bonds, in the order of their (first site,
+ * second site) positions. */
 int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order, int nsteps);
 
 /* Re-compress the whole MPS to bond dimension chi <= chi_max by a left-to-right sequential SVD
@@ -138,8 +167,9 @@ int mpsgb_step(mpsgb_handle h, double J, double hx, double dt, int trotter_order
  * by every truncation fidelity.  Errors: EINVAL for chi < 1 or > chi_max. */
 int mpsgb_truncate(mpsgb_handle h, int chi);
 
-/* Expectation value (Eq. Z_tot, Eq. z2_tot, or <X_tot> = (1/n) sum_j <X_j>) of the current,
- * normalised MPS, written to the host double *out.  Synchronises the handle's stream. */
+/* Expectation value (Eq. Z_tot, Eq. z2_tot, <X_tot> = (1/n) sum_j <X_j>, or <X_stag^2> of Eq.
+ * xy_signal) of the current, normalised MPS, written to the host double *out.  Synchronises the
+ * handle's stream. */
 int mpsgb_expect(mpsgb_handle h, mpsgb_obs obs, double* out);
 
 /* All three observables and the squared norm in one environment sweep:

@@ -19,6 +19,12 @@ layout       row grouping into blocks, snake order, bond bounds, gate schedule.
 statevector  exact state-vector Trotter simulator (<= 24 qubits).
 mps          plain MPS TEBD: dense SVD truncation per bond (numpy/LAPACK).
 rescale      F and F^gamma rescaling, gamma_fit table.
+xy           the XY-model workload of the Supplemental Material (open grid, one qubit per
+             site, depth-7 Trotter step, Eq. xy_init, the signal of Eq. xy_signal): state
+             vector and TEBD by SWAP routing.
+
+The 3D variant (Supplemental Material, 3D TFIM section) is in model / layout / statevector / mps
+(the ``Lz`` arguments).
 
 Every function either has a pin in ``tests/test_oracle_*.py`` (closed forms,
 symmetries, brute force, a library routine) or says "parity unpinned".

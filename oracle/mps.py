@@ -164,19 +164,22 @@ class MPS:
         self.centre = q
 
     # ---------------------------------------------------------------- SWAP routing
-    def _two_site(self, m, swap=False, phase=None, centre_left=True):
+    def _two_site(self, m, swap=False, phase=None, centre_left=True, gate=None):
         """Two-site update of blocks m, m+1 (the centre on one of them): theta = A B as a dense
         (left, d_m, d_m+1, right) tensor, optionally with a diagonal two-qubit phase on the two
         physical indices or with the two physical legs exchanged (a SWAP of the blocks), then the
         SVD of theta as a (left * d) x (d' * right) matrix with numpy.linalg.svd, truncated like
         the MPO sweep (min(chi, numerical rank) values, f = kept / total, renormalised).  The
-        kept singular values go into block m (centre_left) or block m+1."""
+        kept singular values go into block m (centre_left) or block m+1.  `gate`: a general
+        (d_m d_m+1) x (d_m d_m+1) matrix on the two physical indices instead of a phase."""
         A, B = self.blocks[m], self.blocks[m + 1]
         l, da, _ = A.shape
         _, db, r = B.shape
         th = np.tensordot(A, B, axes=([2], [0]))  # (l, da, db, r)
         if phase is not None:
             th = th * phase[None, :, :, None]
+        if gate is not None:
+            th = np.einsum("xy,lyr->lxr", gate, th.reshape(l, da * db, r)).reshape(l, da, db, r)
         if swap:
             th = th.transpose(0, 2, 1, 3)
             da, db = db, da
@@ -305,16 +308,20 @@ class MPS:
         return s
 
 
-def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0, Lz=None):
+def random_canonical(Lx, Ly, chi, seed, decay=None, centre=0, Lz=None, sites=None):
     """Seeded random MPS with every bond at min(chi, bound), in canonical form with the
     orthogonality centre on block `centre`, unit norm.  Entries are complex normal; with `decay`
     every block is scaled by exp(-b / decay) along its right bond index b, so that the Schmidt
     spectra fall off over the bond (a uniformly random state has nearly flat spectra).  The gauge
     moves are this module's QR / LQ steps.  An input generator for generic states: it computes
     nothing of the method and has no pin of its own (its outputs are checked for canonical form
-    and norm where they are used).  Lz: layer count of the open 3D grid (one qubit per site)."""
+    and norm where they are used).  Lz: layer count of the open 3D grid (one qubit per site);
+    sites: an explicit list of sites in MPS order (dicts with "qubits" and "d"), e.g. oracle.xy.blocks."""
     rng = np.random.default_rng(seed)
     m = MPS(Lx, Ly, chi, 0.3, Lz=Lz)
+    if sites is not None:
+        m.layout = [dict(b) for b in sites]
+        m.n = sum(len(b["qubits"]) for b in sites)
     ds = [b["d"] for b in m.layout]
     bd = [1] + [int(min(chi, b)) for b in layout.bond_bounds(Lx, Ly, m.layout)] + [1]
     blocks = []

@@ -51,6 +51,12 @@ int check_config(const mpsgb_config* c) {
   mpsgb::Layout L;
   std::string err;
   if (!mpsgb::make_layout(*c, L, err)) return fail(MPSGB_EINVAL, err);
+  if (c->model != MPSGB_MODEL_TFIM && c->model != MPSGB_MODEL_XY) return fail(MPSGB_EINVAL, "unknown model");
+  if (c->model == MPSGB_MODEL_XY) {
+    if (c->lattice != MPSGB_LATTICE_2D_SITES) return fail(MPSGB_EINVAL, "the XY model runs on LATTICE_2D_SITES");
+    if (c->route != MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "the XY model's gates are routed by SWAP");
+    if (c->trotter_order != 2) return fail(MPSGB_EINVAL, "the XY model's Trotter step is second order");
+  }
   return MPSGB_OK;
 }
 
@@ -99,8 +105,12 @@ int mpsgb_create(const mpsgb_config* cfg, const mpsgb_allocator* alloc, void* cu
 int mpsgb_apply_layer(mpsgb_handle h, mpsgb_layer layer, double angle) {
   if (!h || !h->e) return fail(MPSGB_EINVAL, "null handle");
   if (!std::isfinite(angle)) return fail(MPSGB_EINVAL, "angle is not finite");
-  if (layer != MPSGB_LAYER_X && layer != MPSGB_LAYER_ZZ) return fail(MPSGB_EINVAL, "unknown layer");
-  return guarded([&]() -> int { return layer == MPSGB_LAYER_X ? h->e->apply_x(angle) : h->e->apply_zz(angle); });
+  if (layer != MPSGB_LAYER_X && layer != MPSGB_LAYER_ZZ && layer != MPSGB_LAYER_ZSTAG)
+    return fail(MPSGB_EINVAL, "unknown layer");
+  return guarded([&]() -> int {
+    if (layer == MPSGB_LAYER_ZSTAG) return h->e->apply_zstag(angle);
+    return layer == MPSGB_LAYER_X ? h->e->apply_x(angle) : h->e->apply_zz(angle);
+  });
 }
 
 int mpsgb_apply_gates(mpsgb_handle h, int first, int count, double phi) {
@@ -129,7 +139,8 @@ int mpsgb_observables(mpsgb_handle h, double out[4]) {
 
 int mpsgb_expect(mpsgb_handle h, mpsgb_obs obs, double* out) {
   if (!h || !h->e || !out) return fail(MPSGB_EINVAL, "null argument");
-  if (obs < MPSGB_Z_TOT || obs > MPSGB_X_TOT) return fail(MPSGB_EINVAL, "unknown observable");
+  if (obs < MPSGB_Z_TOT || obs > MPSGB_X_STAG2) return fail(MPSGB_EINVAL, "unknown observable");
+  if (obs == MPSGB_X_STAG2) return guarded([&]() -> int { return h->e->x_stag2(out); });
   double v[4];
   int s = mpsgb_observables(h, v);
   if (s) return s;

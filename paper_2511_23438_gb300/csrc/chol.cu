@@ -153,7 +153,7 @@ int chol_inv(cudaStream_t st, int n, Cx<R>* A, long long lda, Cx<R>* Ci, long lo
   GraphKey key{{1, n, (long long)sizeof(R), (long long)(uintptr_t)A, lda, (long long)(uintptr_t)Ci, ldi,
                 (long long)(uintptr_t)ws, (long long)(uintptr_t)flag, (long long)(rel * 1e18),
                 (long long)(uintptr_t)st, 0}};
-  return replay_or_issue(st, key, [&]() { return chol_issue<R>(st, n, A, lda, Ci, ldi, rel, ws, flag); });
+  return replay_or_issue(st, key, [&](cudaStream_t cs) { return chol_issue<R>(cs, n, A, lda, Ci, ldi, rel, ws, flag); });
 }
 
 template int chol_inv<float>(cudaStream_t, int, c64*, long long, c64*, long long, double, void*, int*);

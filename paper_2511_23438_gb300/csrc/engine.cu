@@ -83,6 +83,9 @@ bool make_layout(int Lx, int Ly, Layout& L, std::string& err) {
       }
       L.k[pos] = c1 - c0;
     }
+  L.stag.assign(L.n, 1);
+  for (int r = 0; r < Lx; ++r)
+    for (int c = 0; c < Ly; ++c) L.stag[r * Ly + c] = ((r + c) & 1) ? -1 : 1;
   std::set<std::pair<int, int>> bonds;
   for (int r = 0; r < Lx; ++r)
     for (int c = 0; c < Ly; ++c) {
@@ -118,6 +121,10 @@ bool make_layout_3d(int Lx, int Ly, int Lz, Layout& L, std::string& err) {
   L.qubits.assign(L.N, {});
   L.intra.assign(L.N, {});
   auto qid = [&](int x, int y, int z) { return (z * Lx + x) * Ly + y; };
+  L.stag.assign(L.n, 1);
+  for (int z = 0; z < Lz; ++z)
+    for (int x = 0; x < Lx; ++x)
+      for (int y = 0; y < Ly; ++y) L.stag[qid(x, y, z)] = ((x + y + z) & 1) ? -1 : 1;
   std::vector<int> pos_of(L.n, -1);
   int pos = 0, row = 0;
   for (int z = 0; z < Lz; ++z)
@@ -146,7 +153,53 @@ bool make_layout_3d(int Lx, int Ly, int Lz, Layout& L, std::string& err) {
   return true;
 }
 
+// open Lx x Ly grid, one qubit per site along the row snake; bonds carry their set of the XY
+// model's Trotter step: horizontal bonds starting on an even / odd column (A / B), vertical bonds
+// starting on an even / odd row (C / D)
+bool make_layout_2d_sites(int Lx, int Ly, Layout& L, std::string& err) {
+  if (Lx < 2 || Ly < 2 || Lx > 16 || Ly > 16 || Lx * Ly > 256) {
+    err = "2D one-qubit-per-site grid must have 2 <= Lx, Ly <= 16 and at most 256 qubits";
+    return false;
+  }
+  L = Layout();
+  L.Lx = Lx; L.Ly = Ly; L.n = Lx * Ly; L.N = L.n;
+  L.k.assign(L.N, 1);
+  L.qubits.assign(L.N, {});
+  L.intra.assign(L.N, {});
+  L.stag.assign(L.n, 1);
+  std::vector<int> pos_of(L.n, -1);
+  int pos = 0;
+  for (int r = 0; r < Lx; ++r)
+    for (int i = 0; i < Ly; ++i) {
+      const int c = (r % 2 == 0) ? i : Ly - 1 - i;
+      pos_of[r * Ly + c] = pos;
+      L.qubits[pos].push_back(r * Ly + c);
+      L.stag[r * Ly + c] = ((r + c) & 1) ? -1 : 1;
+      ++pos;
+    }
+  auto add = [&](int a, int b, int set) {
+    const int pa = pos_of[a], pb = pos_of[b];
+    Layout::Gate g = pa < pb ? Layout::Gate{pa, pb, a, b, 0, 0} : Layout::Gate{pb, pa, b, a, 0, 0};
+    g.set = set;
+    L.inter.push_back(g);
+  };
+  for (int r = 0; r < Lx; ++r)
+    for (int c = 0; c < Ly; ++c) {
+      if (c + 1 < Ly) add(r * Ly + c, r * Ly + c + 1, c % 2);
+      if (r + 1 < Lx) add(r * Ly + c, (r + 1) * Ly + c, 2 + r % 2);
+    }
+  finish_layout(L);
+  return true;
+}
+
 bool make_layout(const mpsgb_config& c, Layout& L, std::string& err) {
+  if (c.lattice == MPSGB_LATTICE_2D_SITES) {
+    if (c.Lz != 0 && c.Lz != 1) {
+      err = "the 2D lattice takes Lz = 0 or 1";
+      return false;
+    }
+    return make_layout_2d_sites(c.Lx, c.Ly, L, err);
+  }
   if (c.lattice == MPSGB_LATTICE_2D_GROUPED) {
     if (c.Lz != 0 && c.Lz != 1) {
       err = "the 2D lattice takes Lz = 0 or 1";
@@ -317,8 +370,15 @@ class EngineT : public Engine {
       if (!tcws) throw Fail{MPSGB_ENOMEM, "allocation of tensor-core workspace failed"};
     }
     dims.assign(L.N - 1, 1);
-    double cth = std::cos(c.theta / 2), sth = std::sin(c.theta / 2);
-    for (int b = 0; b < L.N; ++b) init_product<R>(stream, blk[b], L.k[b], cth, sth);
+    if (c.model == MPSGB_MODEL_XY) {  // |Neel>: the ground state of sum_j s_j Z_j (one qubit per site)
+      for (int b = 0; b < L.N; ++b) {
+        const bool one = L.stag[L.qubits[b][0]] > 0;
+        init_product<R>(stream, blk[b], 1, one ? 0.0 : 1.0, one ? 1.0 : 0.0);
+      }
+    } else {
+      double cth = std::cos(c.theta / 2), sth = std::sin(c.theta / 2);
+      for (int b = 0; b < L.N; ++b) init_product<R>(stream, blk[b], L.k[b], cth, sth);
+    }
     centre = 0;
     F = 1.0;
     synchronize("create");
@@ -400,7 +460,22 @@ class EngineT : public Engine {
     return c;
   }
 
+  int apply_zstag(double alpha) override {
+    std::vector<std::vector<std::complex<double>>> U(L.N);
+    for (int b = 0; b < L.N; ++b) {
+      const int k = L.k[b], dd = 1 << k;
+      U[b].assign((size_t)dd * dd, 0.0);
+      for (int sidx = 0; sidx < dd; ++sidx) {
+        double e = 0;
+        for (int t = 0; t < k; ++t) e += L.stag[L.qubits[b][t]] * (1 - 2 * ((sidx >> (k - 1 - t)) & 1));
+        U[b][(size_t)sidx * dd + sidx] = std::exp(std::complex<double>(0, -alpha * e));
+      }
+    }
+    upload_and_apply(U);
+    return MPSGB_OK;
+  }
   int apply_x(double alpha) override {
+    if (cfg.model == MPSGB_MODEL_XY) throw Fail{MPSGB_EINVAL, "an X layer is not a layer of the XY model"};
     std::vector<std::vector<std::complex<double>>> U(L.N);
     for (int b = 0; b < L.N; ++b) U[b] = rx_kron(L.k[b], alpha);
     upload_and_apply(U);
@@ -417,11 +492,13 @@ class EngineT : public Engine {
     upload_and_apply(U);
   }
   int apply_zz(double phi) override {
+    if (cfg.model == MPSGB_MODEL_XY) throw Fail{MPSGB_EINVAL, "a ZZ layer is not a layer of the XY model"};
     apply_intra(phi, 0.0);
     inter_layer(phi);
     return MPSGB_OK;
   }
   int apply_gates(int first, int count, double phi) override {
+    if (cfg.model == MPSGB_MODEL_XY) throw Fail{MPSGB_EINVAL, "ZZ gates are not gates of the XY model"};
     if (first < 0 || count < 0 || first + count > (int)L.inter.size())
       throw Fail{MPSGB_EINVAL, "gate range outside the schedule"};
     last_f_min = 1.0;
@@ -432,7 +509,33 @@ class EngineT : public Engine {
     last_f_min = 1.0;
     for (auto& g : L.inter) any_gate(g, phi);
   }
+  // the XY model's two-qubit factor exp(-i theta (X X + Y Y)): the identity on |00>, |11> and
+  // cos(2 theta) - i sin(2 theta) X on the span of |01>, |10>
+  static Gate4 xy_gate(double theta) {
+    Gate4 u{};
+    for (int i = 0; i < 4; ++i) u.re[5 * i] = 1.0;
+    const double c = std::cos(2 * theta), sn = std::sin(2 * theta);
+    u.re[5] = u.re[10] = c;
+    u.im[6] = u.im[9] = -sn;
+    return u;
+  }
+  // Eq. xy_trotter_step: sets A, B, C at half duration, D whole, C, B, A at half duration
+  void xy_step(double g, double dt) {
+    static const int sets[7] = {0, 1, 2, 3, 2, 1, 0};
+    static const double w[7] = {0.5, 0.5, 0.5, 1.0, 0.5, 0.5, 0.5};
+    last_f_min = 1.0;
+    for (int l = 0; l < 7; ++l) {
+      const Gate4 u = xy_gate(0.5 * g * dt * w[l]);
+      for (auto& gt : L.inter)
+        if (gt.set == sets[l]) gate_general(gt, u);
+    }
+  }
   int step(double J, double hx, double dt, int order, int nsteps) override {
+    if (cfg.model == MPSGB_MODEL_XY) {
+      if (order != 2) throw Fail{MPSGB_EINVAL, "the XY model's Trotter step is second order"};
+      for (int s = 0; s < nsteps; ++s) xy_step(J, dt);
+      return MPSGB_OK;
+    }
     double alpha = order == 2 ? 0.5 * hx * dt : hx * dt, phi = J * dt;
     for (int s = 0; s < nsteps; ++s) {
       apply_intra(phi, alpha);  // X(alpha) then in-block ZZ phases, fused into one pass per block
@@ -566,7 +669,8 @@ class EngineT : public Engine {
   // of block m, shift_b of block m+1) or with the physical legs exchanged (the blocks swap places),
   // then its SVD truncated to min(chi, numerical rank) values, f = kept / total, renormalised; the
   // singular values go into block m (centre_left) or block m+1.
-  void two_site(int m, bool swap, bool with_phase, double phi, int shift_a, int shift_b, bool centre_left) {
+  void two_site(int m, bool swap, bool with_phase, double phi, int shift_a, int shift_b, bool centre_left,
+                const Gate4* gate4 = nullptr) {
     ar.off = 0;
     const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
     const int l = left(m), da = d(m), mid = dims[m], db = d(m + 1), r = right(m + 1);
@@ -576,6 +680,7 @@ class EngineT : public Engine {
     mm((int)rowsA, (int)colsB, mid, one, rowmajor<R>(blk[m], mid), rowmajor<R>(blk[m + 1], colsB), zero,
        rowmajor<R>(Th, colsB));
     if (with_phase) two_site_phase<R>(stream, l, da, db, r, Th, phi, shift_a, shift_b);
+    if (gate4) two_site_gate<R>(stream, l, da, db, r, Th, *gate4, shift_a, shift_b);
     C* X = Th;
     int prow = (int)rowsA, pcol = (int)colsB;
     if (swap) {
@@ -621,6 +726,16 @@ class EngineT : public Engine {
     move_centre(q);
     for (int m = q - 1; m > p; --m) two_site(m, true, false, 0.0, 0, 0, true);
     two_site(p, false, true, phi, kpos[p] - 1 - g.ti, kpos[p + 1] - 1 - g.tj, false);
+    for (int m = p + 1; m < q; ++m) two_site(m, true, false, 0.0, 0, 0, false);
+    centre = q;
+    stats.gates++;
+  }
+  // a general two-qubit gate between blocks p < q by SWAP routing (the XY model's gates)
+  void gate_general(const Layout::Gate& g, const Gate4& u) {
+    const int p = g.p, q = g.q;
+    move_centre(q);
+    for (int m = q - 1; m > p; --m) two_site(m, true, false, 0.0, 0, 0, true);
+    two_site(p, false, false, 0.0, kpos[p] - 1 - g.ti, kpos[p + 1] - 1 - g.tj, false, &u);
     for (int m = p + 1; m < q; ++m) two_site(m, true, false, 0.0, 0, 0, false);
     centre = q;
     stats.gates++;
@@ -1051,6 +1166,47 @@ class EngineT : public Engine {
     out[1] = h[2].x / (n * n * norm);
     out[2] = h[3].x / (n * norm);
     out[3] = norm;
+    return MPSGB_OK;
+  }
+
+  // <X_stag^2> = (1/n^2) <(sum_j s_j X_j)^2> by the same left-to-right sweep with three
+  // environments: norm, first moment (sum over the blocks so far of O_b) and second moment, where
+  // O_b = sum_{j in b} s_j X_j; per block Y2 <- Y2 + 2 O(Y1) + O(O(Y0)), Y1 <- Y1 + O(Y0)
+  int x_stag2(double* out) override {
+    ar.off = 0;
+    const C one = cmake<R>(1, 0), zero = cmake<R>(0, 0);
+    C* Y[3];
+    for (int i = 0; i < 3; ++i) Y[i] = ar.take<C>((size_t)cap);
+    C* T = ar.take<C>((size_t)cap);
+    C* Ecur[3];
+    C* Enew[3];
+    long long c2 = (long long)chi_eff * chi_eff;
+    for (int i = 0; i < 3; ++i) { Ecur[i] = ar.take<C>(c2); Enew[i] = ar.take<C>(c2); }
+    if (!Enew[2]) throw Fail{MPSGB_ENOMEM, "workspace exhausted in observables"};
+    set_identity<R>(stream, 1, Ecur[0], 1);
+    for (int i = 1; i < 3; ++i) set_zero<R>(stream, 1, Ecur[i]);
+    for (int b = 0; b < L.N; ++b) {
+      const int l = left(b), dd = d(b), r = right(b), k = L.k[b];
+      long long row = (long long)dd * r;
+      int neg = 0;
+      for (int t = 0; t < k; ++t)
+        if (L.stag[L.qubits[b][t]] < 0) neg |= 1 << (k - 1 - t);
+      for (int i = 0; i < 3; ++i)
+        mm(l, (int)row, l, one, rowmajor<R>(Ecur[i], l), rowmajor<R>(blk[b], row), zero, rowmajor<R>(Y[i], row));
+      stag_x<R>(stream, 1, l, dd, r, Y[2], Y[1], Y[2], 2.0, neg);
+      stag_x<R>(stream, 1, l, dd, r, nullptr, Y[0], T, 1.0, neg);
+      stag_x<R>(stream, 1, l, dd, r, Y[2], T, Y[2], 1.0, neg);
+      stag_x<R>(stream, 0, l, dd, r, Y[1], T, Y[1], 1.0, 0);
+      for (int i = 0; i < 3; ++i)
+        mm(r, r, l * dd, one, transposed<R>(blk[b], r, true), rowmajor<R>(Y[i], r), zero, rowmajor<R>(Enew[i], r));
+      for (int i = 0; i < 3; ++i) std::swap(Ecur[i], Enew[i]);
+    }
+    C h[3];
+    for (int i = 0; i < 3; ++i) cudaMemcpyAsync(&h[i], Ecur[i], sizeof(C), cudaMemcpyDeviceToHost, stream);
+    synchronize("observables");
+    if (tc) check_device_error();
+    const double n = L.n;
+    *out = h[2].x / (n * n * h[0].x);
     return MPSGB_OK;
   }
 

@@ -20,8 +20,12 @@ struct Fail {
 // mps_drawing), or one qubit per site along the 3D snake of an open Lx x Ly x Lz grid (the
 // Supplemental Material's 3D TFIM section, Fig. 3D_snake).
 struct Layout {
-  struct Gate { int p, q, qi, qj, ti, tj; };  // block positions p < q, global qubits, bit positions (0 = MSB)
+  struct Gate {
+    int p, q, qi, qj, ti, tj;  // block positions p < q, global qubits, bit positions (0 = MSB)
+    int set = -1;              // bond set A..D (0..3) of the XY model's Trotter step, -1 elsewhere
+  };
   int Lx = 0, Ly = 0, Lz = 1, N = 0, n = 0;
+  std::vector<int> stag;                               // staggered sign s_j (+1 / -1) per global qubit
   std::vector<int> k;                                  // qubits per block
   std::vector<std::vector<int>> qubits;                // global qubit ids per block, MSB first
   std::vector<std::vector<std::pair<int, int>>> intra; // in-block ZZ pairs (bit positions)
@@ -54,6 +58,8 @@ class Engine {
   virtual int save(const char* path) = 0;
   virtual int load_blocks(FILE* fh) = 0;
   virtual int sync() = 0;
+  virtual int apply_zstag(double alpha) = 0;                   // prod_j exp(-i alpha s_j Z_j)
+  virtual int x_stag2(double* out) = 0;                        // <X_stag^2> (Eq. xy_signal)
   double F = 1.0;                     // F_MPS: product of all truncation fidelities
   double last_f_min = 1.0;            // smallest truncation fidelity of the last layer
   Stats stats;

@@ -4,7 +4,10 @@
 // given buffers (the Cholesky recursion, the eigensolver's orthonormalisation and back-
 // transformation), most of them small.  On a capturable stream such a sequence is recorded once
 // per key as a CUDA graph and replayed afterwards, which takes the host launch cost and most gaps
-// off the device timeline.  One cache serves the process (at most 512 graphs, the least recently
+// off the device timeline.  The recording is made on a stream private to the calling host thread
+// (nothing runs during a recording, and no other thread's launches onto the caller's stream can
+// enter it, also where several handles share one stream); the graph is then launched on the
+// caller's stream, after the work already issued there.  One cache serves the process (at most 512 graphs, the least recently
 // used dropped first); a key holds the stream and every buffer address, and one handle's work runs
 // on one host thread at a time, so no graph is launched from two threads at once.  The legacy
 // default stream cannot be captured and a stream that is already capturing is not nested into:
@@ -56,17 +59,31 @@ void release_all() {
 }
 constexpr size_t kMaxGraphs = 512;
 thread_local bool t_graphs = true;
+
+// the calling thread's capture stream, created on first use and destroyed with the thread
+struct CaptureStream {
+  cudaStream_t s = nullptr;
+  ~CaptureStream() {
+    if (s) cudaStreamDestroy(s);
+  }
+  cudaStream_t get() {
+    if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+    return s;
+  }
+};
+thread_local CaptureStream t_capture;
 }  // namespace
 
 void set_graphs_enabled(bool on) { t_graphs = on; }
 bool graphs_enabled() { return t_graphs; }
 
-int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int()>& issue) {
+int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int(cudaStream_t)>& issue) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   const bool capturable = t_graphs && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread &&
                           !g_kt_enabled && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
-  if (!capturable) {
-    if (issue() != 0) return -4;
+  cudaStream_t cap = capturable ? t_capture.get() : nullptr;
+  if (!cap) {
+    if (issue(st) != 0) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
   }
   Cache& c = cache();
@@ -81,13 +98,13 @@ int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<in
         return 0;
       }
   }
-  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -4;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -4;
   unsigned long long kernels = 0;  // the captured kernels run (and are counted) at each graph launch
   t_launch_sink = &kernels;
-  const int issued = issue();
+  const int issued = issue(cap);
   t_launch_sink = nullptr;
   cudaGraph_t graph = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+  const cudaError_t ec = cudaStreamEndCapture(cap, &graph);
   if (issued != 0 || ec != cudaSuccess || !graph) {
     if (graph) cudaGraphDestroy(graph);
     cudaGetLastError();

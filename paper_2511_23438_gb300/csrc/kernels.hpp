@@ -19,7 +19,10 @@ struct GraphKey {
 // Issue the launch sequence `issue` (which returns 0, or non-zero on a failed call) on st: on a
 // capturable stream it is recorded once per key as a CUDA graph and replayed; otherwise issued
 // directly.  Returns 0, or -4 if a call or the capture failed.
-int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int()>& issue);
+// Runs issue(s) once: directly on st (s = st), or the first time for `key` recorded as a CUDA graph on
+// a capture stream private to the calling thread (s = that stream, so that no other thread's work on
+// st can enter the recording) and launched on st; later calls with the same key launch the graph.
+int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int(cudaStream_t)>& issue);
 // graph replay for the calling host thread (on by default)
 void set_graphs_enabled(bool on);
 bool graphs_enabled();
@@ -101,6 +104,12 @@ void scale_rows(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, con
 // z_b likewise of the second (the gate of a two-site update)
 template <typename R>
 void two_site_phase(cudaStream_t st, int l, int da, int db, int r, Cx<R>* th, double phi, int shift_a, int shift_b);
+// a 4 x 4 two-qubit gate (row-major, index 2 x + y with x the first qubit's bit), by value
+struct Gate4 {
+  double re[16], im[16];
+};
+template <typename R>
+void two_site_gate(cudaStream_t st, int l, int da, int db, int r, Cx<R>* th, const Gate4& u, int shift_a, int shift_b);
 // X[:rows, j] *= c s[j] for j < cols (s: device FP64)
 template <typename R>
 void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c);
@@ -142,6 +151,11 @@ void scale_cols_pow(cudaStream_t st, int nrow, int ncol, Cx<R>* M, long long ld,
 template <typename R>
 void weighted_phys(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* Y1, const Cx<R>* Y0, Cx<R>* Z,
                    double coef);
+// Z = Y1 + coef * O(Y0) over (l, d, r): O = identity (mode 0) or sum_t s_t X_t over the block's
+// qubits (mode 1; s_t = -1 where bit t of negmask is set, bit 0 = least significant); Y1 may be null
+template <typename R>
+void stag_x(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* Y1, const Cx<R>* Y0, Cx<R>* Z, double coef,
+            int negmask);
 // sum_ij conj(X_ij) * Y_ij accumulated in FP64 into out[0..1] (re, im) -- device pointer
 template <typename R>
 void dot_fp64(cudaStream_t st, long long n, const Cx<R>* X, const Cx<R>* Y, double* out);

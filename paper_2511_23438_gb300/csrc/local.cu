@@ -129,6 +129,32 @@ __global__ void weighted_phys_kernel(int mode, int l, int d, int r, const Cx<R>*
   }
 }
 
+// Z = Y1 + coef * O(Y0) over a block-shaped tensor (l, d, r): mode 0, O = identity; mode 1,
+// O = sum_t s_t X_t (bit flips of the physical index, s_t = -1 where bit t of negmask is set)
+template <typename R>
+__global__ void stag_x_kernel(int mode, int l, int d, int r, const Cx<R>* Y1, const Cx<R>* Y0, Cx<R>* Z, double coef,
+                              int negmask) {
+  long long tot = (long long)l * d * r;
+  int k = 31 - __clz(d);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    long long a = e / ((long long)d * r);
+    long long rem = e - a * (long long)d * r;
+    int s = (int)(rem / r);
+    long long b = rem - (long long)s * r;
+    Cx<R> v = Y1 ? Y1[e] : cmake<R>(0, 0);
+    Cx<R> acc = cmake<R>(0, 0);
+    if (mode == 0) {
+      acc = Y0[e];
+    } else {
+      for (int t = 0; t < k; ++t) {
+        const Cx<R> y = Y0[(a * d + (s ^ (1 << t))) * (long long)r + b];
+        acc = ((negmask >> t) & 1) ? acc - y : acc + y;
+      }
+    }
+    Z[e] = v + (R)coef * acc;
+  }
+}
+
 template <typename R>
 __global__ void dot_fp64_kernel(long long n, const Cx<R>* X, const Cx<R>* Y, double* out) {
   double re = 0, im = 0;
@@ -275,6 +301,14 @@ void scale_cols_pow(cudaStream_t st, int nrow, int ncol, Cx<R>* M, long long ld,
 }
 
 template <typename R>
+void stag_x(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* Y1, const Cx<R>* Y0, Cx<R>* Z, double coef,
+            int negmask) {
+  long long tot = (long long)l * d * r;
+  stag_x_kernel<R><<<nblocks(tot, 256), 256, 0, st>>>(mode, l, d, r, Y1, Y0, Z, coef, negmask);
+  count_launch();
+}
+
+template <typename R>
 void weighted_phys(cudaStream_t st, int mode, int l, int d, int r, const Cx<R>* Y1, const Cx<R>* Y0, Cx<R>* Z,
                    double coef) {
   long long tot = (long long)l * d * r;
@@ -335,6 +369,7 @@ void block_diag2(cudaStream_t st, int r, const Cx<R>* P, const Cx<R>* Q, Cx<R>* 
   template void axpby<R>(cudaStream_t, int, int, Cx<R>, View<R>, Cx<R>, View<R>, View<R>);                   \
   template void scale_cols_pow<R>(cudaStream_t, int, int, Cx<R>*, long long, const R*, int);                 \
   template void weighted_phys<R>(cudaStream_t, int, int, int, int, const Cx<R>*, const Cx<R>*, Cx<R>*, double); \
+  template void stag_x<R>(cudaStream_t, int, int, int, int, const Cx<R>*, const Cx<R>*, Cx<R>*, double, int);    \
   template void dot_fp64<R>(cudaStream_t, long long, const Cx<R>*, const Cx<R>*, double*);                   \
   template void trace_fp64<R>(cudaStream_t, int, const Cx<R>*, long long, double*);                          \
   template void set_identity<R>(cudaStream_t, int, Cx<R>*, long long);                                       \

@@ -300,6 +300,43 @@ __global__ void two_site_phase_kernel(int l, int da, int db, int r, Cx<R>* th, d
   }
 }
 
+// insert a zero bit at position pos of v
+__device__ __forceinline__ int insert_zero_bit(int v, int pos) {
+  return ((v >> pos) << (pos + 1)) | (v & ((1 << pos) - 1));
+}
+
+// th (l, da, db, r): a general two-qubit gate u on bit shift_a of the first physical index and bit
+// shift_b of the second (u's row / column index 2 x + y, x the first qubit's bit); one thread per
+// group of the four amplitudes that differ only in those two bits
+template <typename R>
+__global__ void two_site_gate_kernel(int l, int da, int db, int r, Cx<R>* th, Gate4 u, int shift_a, int shift_b) {
+  const int ha = da >> 1, hb = db >> 1;
+  const long long tot = (long long)l * ha * hb * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e % r;
+    const long long q = e / r;
+    const int tr = (int)(q % hb);
+    const int sr = (int)((q / hb) % ha);
+    const long long a = q / ((long long)hb * ha);
+    const int s0 = insert_zero_bit(sr, shift_a), t0 = insert_zero_bit(tr, shift_b);
+    long long idx[4];
+    Cx<R> x[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int s = s0 | ((v >> 1) << shift_a), t = t0 | ((v & 1) << shift_b);
+      idx[v] = ((a * da + s) * db + t) * r + b;
+      x[v] = th[idx[v]];
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      Cx<R> acc = cmake<R>(0, 0);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cfma(acc, cmake<R>((R)u.re[4 * w + v], (R)u.im[4 * w + v]), x[v]);
+      th[idx[w]] = acc;
+    }
+  }
+}
+
 // X[i, j] *= c * s[i] for i < rows, j < cols
 template <typename R>
 __global__ void scale_rows_kernel(int rows, int cols, Cx<R>* X, long long ld, const double* s, double c) {
@@ -480,6 +517,13 @@ void two_site_phase(cudaStream_t st, int l, int da, int db, int r, Cx<R>* th, do
 }
 
 template <typename R>
+void two_site_gate(cudaStream_t st, int l, int da, int db, int r, Cx<R>* th, const Gate4& u, int shift_a, int shift_b) {
+  two_site_gate_kernel<R><<<grid_of((long long)l * (da >> 1) * (db >> 1) * r, 256), 256, 0, st>>>(l, da, db, r, th, u,
+                                                                                                 shift_a, shift_b);
+  count_launch();
+}
+
+template <typename R>
 void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c) {
   scale_cols_kernel<R><<<grid_of((long long)rows * cols, 256), 256, 0, st>>>(rows, cols, X, ld, s, c);
   count_launch();
@@ -491,7 +535,8 @@ void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, con
   template void mpo_expand<R>(cudaStream_t, int, int, int, int, const Cx<R>*, Cx<R>*, double, int);                 \
   template void scale_rows<R>(cudaStream_t, int, int, Cx<R>*, long long, const double*, double);              \
   template void scale_cols<R>(cudaStream_t, int, int, Cx<R>*, long long, const double*, double);             \
-  template void two_site_phase<R>(cudaStream_t, int, int, int, int, Cx<R>*, double, int, int);
+  template void two_site_phase<R>(cudaStream_t, int, int, int, int, Cx<R>*, double, int, int);                    \
+  template void two_site_gate<R>(cudaStream_t, int, int, int, int, Cx<R>*, const Gate4&, int, int);
 MPSGB_SVD_INST(double)
 MPSGB_SVD_INST(float)
 

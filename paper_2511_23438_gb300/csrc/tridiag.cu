@@ -802,43 +802,43 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
     // CUDA graph where possible
     GraphKey key{{2, n, nvec, (long long)sizeof(R), (long long)(uintptr_t)workspace, (long long)(uintptr_t)V, ldv,
                   (long long)(uintptr_t)st, 0, 0, 0, 0}};
-    const int bt = replay_or_issue(st, key, [&]() -> int {
+    const int bt = replay_or_issue(st, key, [&](cudaStream_t cs) -> int {
     for (int b0 = 0; b0 < nvec; b0 += 64) {
       const int nb = std::min(64, nvec - b0);
       R* Zb = Z + b0;
       for (int pass = 0; pass < 2 && b0 > 0; ++pass) {
-        rgemm<R>(st, b0, nb, n, R(1), Z, n, true, Zb, n, false, R(0), Cr, nb, Wr, wr_elems);
-        rgemm<R>(st, n, nb, b0, R(-1), Z, n, false, Cr, nb, false, R(1), Zb, n, Wr, wr_elems);
+        rgemm<R>(cs, b0, nb, n, R(1), Z, n, true, Zb, n, false, R(0), Cr, nb, Wr, wr_elems);
+        rgemm<R>(cs, n, nb, b0, R(-1), Z, n, false, Cr, nb, false, R(1), Zb, n, Wr, wr_elems);
       }
       for (int pass = 0; pass < 2; ++pass) {
-        rgemm<R>(st, nb, nb, n, R(1), Zb, n, true, Zb, n, false, R(0), Sr, nb, Wr, wr_elems);
-        chol_inv_kernel<R><<<1, 256, ci_smem, st>>>(nb, Sr, Tr, d_err + 1);
-        right_mul_inplace_kernel<R><<<(n + (sizeof(R) == 8 ? 15 : 63)) / (sizeof(R) == 8 ? 16 : 64), 256, 0, st>>>(
+        rgemm<R>(cs, nb, nb, n, R(1), Zb, n, true, Zb, n, false, R(0), Sr, nb, Wr, wr_elems);
+        chol_inv_kernel<R><<<1, 256, ci_smem, cs>>>(nb, Sr, Tr, d_err + 1);
+        right_mul_inplace_kernel<R><<<(n + (sizeof(R) == 8 ? 15 : 63)) / (sizeof(R) == 8 ? 16 : 64), 256, 0, cs>>>(
             n, nb, Zb, n, Tr);
         count_launch(2);
       }
     }
-      real_to_complex_kernel<R><<<1024, 256, 0, st>>>(nn_, Z, X);
+      real_to_complex_kernel<R><<<1024, 256, 0, cs>>>(nn_, Z, X);
     count_launch();
     const Cx<R> one = cmake<R>(1, 0), zero = cmake<R>(0, 0), mone = cmake<R>(-1, 0);
     const int nref = n - 1;
     for (int i0 = ((nref - 1) / NB) * NB; i0 >= 0; i0 -= NB) {
       const int nb = std::min(NB, nref - i0);
       const int m = n - i0 - 1;
-      panel_kernel<R><<<256, 256, 0, st>>>(n, i0, nb, Wm, Pn);
+      panel_kernel<R><<<256, 256, 0, cs>>>(n, i0, nb, Wm, Pn);
       count_launch();
       // S = V^H V, T from S, Y = V^H X, Y2 = T Y, X -= V Y2
-      gemm_splitk<R>(st, nb, nb, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Pn, nb), zero, rowmajor<R>(Sm, nb),
+      gemm_splitk<R>(cs, nb, nb, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Pn, nb), zero, rowmajor<R>(Sm, nb),
                      Wc, wc_elems);
-      wy_t_kernel<R><<<1, 32, 0, st>>>(nb, Sm, tau + i0, Tm);
+      wy_t_kernel<R><<<1, 32, 0, cs>>>(nb, Sm, tau + i0, Tm);
       count_launch();
       Cx<R>* Xs = X + (long long)(i0 + 1) * n;
-      gemm_splitk<R>(st, nb, nvec, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n),
+      gemm_splitk<R>(cs, nb, nvec, m, one, transposed<R>(Pn, nb, true), rowmajor<R>(Xs, n), zero, rowmajor<R>(Y1, n),
                      Wc, wc_elems);
-      gemm<R>(st, nb, nvec, nb, one, rowmajor<R>(Tm, nb), rowmajor<R>(Y1, n), zero, rowmajor<R>(Y2, n));
-      gemm<R>(st, m, nvec, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
+      gemm<R>(cs, nb, nvec, nb, one, rowmajor<R>(Tm, nb), rowmajor<R>(Y1, n), zero, rowmajor<R>(Y2, n));
+      gemm<R>(cs, m, nvec, nb, mone, rowmajor<R>(Pn, nb), rowmajor<R>(Y2, n), one, rowmajor<R>(Xs, n));
     }
-    copy_view<R, R>(st, n, nvec, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
+    copy_view<R, R>(cs, n, nvec, rowmajor<R>(X, n), rowmajor<R>(V, ldv));
     return 0;
     });
     if (bt != 0) return -4;

@@ -13,9 +13,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmpsgb.so")
 FP64, SPLIT_TF32X3, SPLIT_BF16X3, FP32 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "split_tf32x3": SPLIT_TF32X3, "split_bf16x3": SPLIT_BF16X3, "fp32": FP32}
 ROUTE_MPO, ROUTE_SWAP = 0, 1
-LATTICE_2D_GROUPED, LATTICE_3D_SITES = 0, 1
-LAYER_X, LAYER_ZZ = 0, 1
-Z_TOT, Z_TOT2, X_TOT = 0, 1, 2
+LATTICE_2D_GROUPED, LATTICE_3D_SITES, LATTICE_2D_SITES = 0, 1, 2
+LAYER_X, LAYER_ZZ, LAYER_ZSTAG = 0, 1, 2
+Z_TOT, Z_TOT2, X_TOT, X_STAG2 = 0, 1, 2, 3
+MODEL_TFIM, MODEL_XY = 0, 1
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ETIMEDOUT", -4: "EDEVICE", -5: "ESTATE"}
 
 
@@ -29,7 +30,7 @@ class Config(ctypes.Structure):
     _fields_ = [("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("chi_max", ctypes.c_int), ("theta", ctypes.c_double),
                 ("prec", ctypes.c_int), ("route", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("J", ctypes.c_double), ("h", ctypes.c_double), ("dt", ctypes.c_double),
-                ("trotter_order", ctypes.c_int), ("lattice", ctypes.c_int), ("Lz", ctypes.c_int)]
+                ("trotter_order", ctypes.c_int), ("lattice", ctypes.c_int), ("Lz", ctypes.c_int), ("model", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -123,9 +124,15 @@ def _check(status):
 
 
 def config(Lx, Ly, chi, theta, prec="fp64", J=-1.0, h=2.0, dt=0.25, order=2, seed=0, route=ROUTE_MPO,
-           lattice=LATTICE_2D_GROUPED, Lz=1):
+           lattice=LATTICE_2D_GROUPED, Lz=1, model=MODEL_TFIM):
     return Config(Lx, Ly, chi, theta, PRECISIONS[prec] if isinstance(prec, str) else prec, route, seed, J, h, dt, order,
-                  lattice, Lz)
+                  lattice, Lz, model)
+
+
+def xy_config(Lx, Ly, chi, g, dt, prec="fp64"):
+    """The XY workload's config: open Lx x Ly grid, one qubit per site, SWAP routing, second order."""
+    return config(Lx, Ly, chi, 0.0, prec=prec, J=g, h=0.0, dt=dt, order=2, route=ROUTE_SWAP,
+                  lattice=LATTICE_2D_SITES, model=MODEL_XY)
 
 
 def convert_checkpoint(src, dst, prec):

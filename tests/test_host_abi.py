@@ -70,6 +70,21 @@ def test_3d_schedule_matches_oracle(lib, dims):
     assert lib.footprint_bytes(cfg) == chi * chi * 2 * Lx * Ly * Lz * 16
 
 
+@pytest.mark.parametrize("dims", [(2, 2), (3, 4), (4, 4), (5, 6), (6, 6)])
+def test_2d_sites_schedule_matches_oracle(lib, dims):
+    # open grid, one qubit per site along the row snake (the XY workload's lattice): the library's
+    # gate list equals the oracle's bond sets A..D merged in (first site, second site) order
+    from oracle import xy
+    Lx, Ly = dims
+    cfg = lib.xy_config(Lx, Ly, 16, 1.0, 0.1)
+    sched = xy.schedule(Lx, Ly)
+    merged = sorted([g for v in sched.values() for g in v], key=lambda g: (g[0], g[1], g[2], g[3]))
+    assert lib.schedule_gates(cfg) == [tuple(g) for g in merged]
+    info = lib.schedule_info(cfg)
+    assert info["blocks"] == Lx * Ly and info["intra"] == 0 and info["dmax"] == 2
+    assert info["inter"] == Lx * (Ly - 1) + (Lx - 1) * Ly
+
+
 def test_host_formulas(lib):
     assert abs(lib.initial_theta(-1.0, 2.0, 0.0) - model.theta_min()) < 1e-15
     assert abs(lib.initial_theta(-1.0, 2.0, 0.0, lattice=lib.LATTICE_2D_GROUPED) - model.theta_min()) < 1e-15
@@ -96,7 +111,12 @@ def test_footprint(lib):
 def test_invalid_arguments_rejected_on_host(lib):
     for cfg in [lib.config(1, 4, 16, 0.1), lib.config(3, 4, 0, 0.1), lib.config(3, 4, 16, float("nan")),
                 lib.config(3, 4, 16, 0.1, prec=7), lib.config(3, 40, 16, 0.1),
-                lib.config(3, 4, 16, 0.1, Lz=2), lib.config(3, 4, 16, 0.1, lattice=2),
+                lib.config(3, 4, 16, 0.1, Lz=2), lib.config(3, 4, 16, 0.1, lattice=3),
+                lib.config(3, 4, 16, 0.1, model=2), lib.config(3, 4, 16, 0.1, model=lib.MODEL_XY),
+                lib.config(3, 4, 16, 0.1, model=lib.MODEL_XY, lattice=lib.LATTICE_2D_SITES),
+                lib.config(3, 4, 16, 0.1, model=lib.MODEL_XY, lattice=lib.LATTICE_2D_SITES, route=lib.ROUTE_SWAP,
+                           order=1),
+                lib.config(17, 4, 16, 0.1, lattice=lib.LATTICE_2D_SITES),
                 lib.config(3, 3, 16, 0.1, lattice=1, Lz=1), lib.config(9, 9, 16, 0.1, lattice=1, Lz=9)]:
         with pytest.raises(lib.MpsgbError) as e:
             lib.MPS(cfg)
