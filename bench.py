@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--peaks", action="store_true", help="measure dense matmul rates (torch) and exit")
     ap.add_argument("--split-error", default="", help="error table of the complex64 forms against the FP64 GPU "
                     "form: comma-separated chi:steps pairs on the 5x6 grid (e.g. 64:20,256:8), then exit")
+    ap.add_argument("--split-perturb", type=float, default=0.0, help="with --split-error: start the compared "
+                    "handle at theta + this value (with --prec fp64: the sensitivity floor of the run)")
     return ap.parse_args()
 
 
@@ -380,11 +382,13 @@ def fp64_form_rate(lib, m_split, Lx, Ly, n_updates, stream):
                       (Lx, Ly, m_split.cfg.chi_max, n)}
 
 
-def split_error_table(spec, prec, Lx=5, Ly=6):
+def split_error_table(spec, prec, Lx=5, Ly=6, perturb=0.0):
     """Error of a complex64 form against the FP64 GPU form (both through the library, the FP64
     form being the one held to 1e-9 of the oracle) on the 5x6 grid (rows 3 + 3, d = 8) from the
     mid-temperature product state: for each chi, `steps` second-order steps side by side, the
-    largest |d<Z_tot>|, |d<Z_tot^2>|, |d<X_tot>| and |dF/F| over the steps."""
+    largest |d<Z_tot>|, |d<Z_tot^2>|, |d<X_tot>| and |dF/F| over the steps.  perturb != 0 starts
+    the compared handle at theta + perturb (with prec fp64 this measures how far a perturbation
+    of that size carries through the truncations of the run)."""
     from paper_2511_23438_gb300 import lib
     lib.load()
     theta = lib.initial_theta(J, HX, TEMP_DTHETA)
@@ -392,7 +396,7 @@ def split_error_table(spec, prec, Lx=5, Ly=6):
     for item in spec.split(","):
         chi, steps = (int(v) for v in item.split(":"))
         a = lib.MPS(lib.config(Lx, Ly, chi, theta, prec="fp64"))
-        b = lib.MPS(lib.config(Lx, Ly, chi, theta, prec=prec))
+        b = lib.MPS(lib.config(Lx, Ly, chi, theta + perturb, prec=prec))
         err = {"Z": 0.0, "Z2": 0.0, "X": 0.0, "F_rel": 0.0}
         t0 = time.perf_counter()
         for _ in range(steps):
@@ -407,7 +411,7 @@ def split_error_table(spec, prec, Lx=5, Ly=6):
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         a.close()
         b.close()
-    return {"split_error": rows, "precision": prec, "grid": "%dx%d" % (Lx, Ly),
+    return {"split_error": rows, "precision": prec, "perturb": perturb, "grid": "%dx%d" % (Lx, Ly),
             "reference": "FP64 GPU form (complex128, exact SVD truncation)"}
 
 
@@ -437,7 +441,7 @@ def main():
         print(json.dumps(measure_peaks()), flush=True)
         return
     if args.split_error:
-        print(json.dumps(split_error_table(args.split_error, args.prec)), flush=True)
+        print(json.dumps(split_error_table(args.split_error, args.prec, perturb=args.split_perturb)), flush=True)
         return
 
     import torch
@@ -567,6 +571,7 @@ def main():
                        "l2": "inputs larger than L2 (MPS resident in HBM, streamed every step)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": launches,
+            "launches_before_timed": l0,
             "bond_updates": int(upd_all),
             "observables": obs,
             "clocks": clk,

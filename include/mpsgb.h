@@ -52,7 +52,8 @@ typedef enum {
  *   FP64         complex128 storage, every contraction in FP64; every spanned bond is truncated by
  *                the SVD of the centre block (one-sided Jacobi, no Gram matrix), which resolves
  *                Schmidt values down to the rounding floor.  The accuracy reference.
- *   SPLIT_TF32X3 reserved (TF32 splits; not available in this build: EINVAL).
+ *   SPLIT_TF32X3 as SPLIT_BF16X3 with TF32 splits on the tensor cores (tcgen05 kind::tf32): x_hi =
+ *                tf32(x), x_lo = tf32(x - x_hi), 22 significant bits, at half the BF16 tensor rate.
  *   SPLIT_BF16X3 complex64 storage; the block-sized contractions (Grams, left factors, new blocks,
  *                transfer and environment products) on the tcgen05 tensor cores: every FP32
  *                component is split into two BF16 terms (hi + lo, 16 significant bits) and a
@@ -257,7 +258,8 @@ const char* mpsgb_kernel_site_name(int site);
 
 /* Self-test of the tensor-core split GEMM (no paper counterpart; a kernel check): multiplies seeded
  * random complex64 matrices, op(A) (M x K) times op(B) (K x N) with op(A) = A^H if mode bit 0 and
- * op(B) = B^T if mode bit 1, on the tensor cores and on FP32 CUDA cores, and writes
+ * op(B) = B^T if mode bit 1, on the tensor cores (BF16 splits, or TF32 splits if mode bit 2) and
+ * on FP32 CUDA cores, and writes
  * max |difference| / max |CUDA-core result| to *rel_err.  Allocates its own device memory. */
 int mpsgb_tc_gemm_selftest(int M, int N, int K, int mode, unsigned long long seed, double* rel_err);
 

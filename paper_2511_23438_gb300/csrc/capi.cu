@@ -45,7 +45,6 @@ int check_config(const mpsgb_config* c) {
   if (!c) return fail(MPSGB_EINVAL, "null config");
   if (c->prec < MPSGB_FP64 || c->prec > MPSGB_FP32) return fail(MPSGB_EINVAL, "unknown precision");
   if (c->route != MPSGB_ROUTE_MPO && c->route != MPSGB_ROUTE_SWAP) return fail(MPSGB_EINVAL, "unknown route");
-  if (c->prec == MPSGB_SPLIT_TF32X3) return fail(MPSGB_EINVAL, "SPLIT_TF32X3 is not available in this build");
   if (!std::isfinite(c->theta)) return fail(MPSGB_EINVAL, "theta is not finite");
   if (c->chi_max < 1 || c->chi_max > 8192) return fail(MPSGB_EINVAL, "chi_max must be in 1..8192");
   mpsgb::Layout L;

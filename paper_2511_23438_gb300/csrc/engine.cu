@@ -262,7 +262,8 @@ class EngineT : public Engine {
   int chi_eff = 1, dmax = 2;
   double tau = 1e-13;  // numerical-rank threshold on squared singular values (relative)
   std::vector<R> hbuf;
-  bool tc = false;        // block-sized contractions on the tensor cores (split form)
+  bool tc = false;        // block-sized contractions on the tensor cores (split forms)
+  bool tc_tf32 = false;   // ... with TF32 splits (kind::tf32) instead of BF16
   void* tcws = nullptr;   // BF16 operand planes of the tensor-core GEMM
   size_t tcws_bytes = 0;
   int* derr = nullptr;    // device error word of bounded waits in kernels
@@ -276,7 +277,7 @@ class EngineT : public Engine {
   void mm(int M, int N, int K, C alpha, View<R> A, View<R> B, C beta, View<R> Cv) {
     if constexpr (std::is_same<R, float>::value) {
       if (tc && M >= 64 && N >= 64 && K >= 64) {
-        int s = tc_gemm(stream, M, N, K, alpha, A, B, beta, Cv, tcws, tcws_bytes, derr);
+        int s = tc_gemm(stream, M, N, K, alpha, A, B, beta, Cv, tcws, tcws_bytes, derr, tc_tf32);
         if (s != 0) throw Fail{MPSGB_EDEVICE, "tensor-core GEMM set-up failed"};
         return;
       }
@@ -365,7 +366,7 @@ class EngineT : public Engine {
     cudaMemsetAsync(derr, 0, sizeof(int) * 4, stream);
     if (tc) {
       // largest operand pair: the Gram of a left factor (2 chi x chi d) with itself
-      tcws_bytes = tc_gemm_workspace_bytes(4LL * chi_eff, 4LL * chi_eff, (long long)chi_eff * dmax) + (1 << 20);
+      tcws_bytes = tc_gemm_workspace_bytes(4LL * chi_eff, 4LL * chi_eff, (long long)chi_eff * dmax, tc_tf32) + (1 << 20);
       tcws = mem.get(tcws_bytes);
       if (!tcws) throw Fail{MPSGB_ENOMEM, "allocation of tensor-core workspace failed"};
     }
@@ -1298,10 +1299,11 @@ Engine* make_engine(const mpsgb_config& cfg, const mpsgb_allocator* alloc, cudaS
       e = x;
       x->exact = true;
       x->init(cfg, alloc, st);
-    } else if (cfg.prec == MPSGB_FP32 || cfg.prec == MPSGB_SPLIT_BF16X3) {
+    } else if (cfg.prec == MPSGB_FP32 || cfg.prec == MPSGB_SPLIT_BF16X3 || cfg.prec == MPSGB_SPLIT_TF32X3) {
       auto* x = new EngineT<float>();
       e = x;
-      x->tc = cfg.prec == MPSGB_SPLIT_BF16X3;
+      x->tc = cfg.prec == MPSGB_SPLIT_BF16X3 || cfg.prec == MPSGB_SPLIT_TF32X3;
+      x->tc_tf32 = cfg.prec == MPSGB_SPLIT_TF32X3;
       x->init(cfg, alloc, st);
     } else {
       throw Fail{MPSGB_EINVAL, "precision not available in this build"};

@@ -115,13 +115,14 @@ template <typename R>
 void scale_cols(cudaStream_t st, int rows, int cols, Cx<R>* X, long long ld, const double* s, double c);
 
 // ---------------------------------------------------------------- tensor-core split GEMM (tcgemm.cu)
-// C = alpha op(A) op(B) + beta C on complex64 views with 2-term BF16 splits on tcgen05
-// (FP32 accumulation).  ws: device workspace of tc_gemm_workspace_bytes(M, N, K) bytes;
-// d_err: device word set non-zero if a bounded wait of the kernel ran out.
-// Returns 0, or < 0 if the workspace is too small / the tensor maps could not be built.
-size_t tc_gemm_workspace_bytes(long long M, long long N, long long K);
+// C = alpha op(A) op(B) + beta C on complex64 views with 2-term splits on tcgen05: BF16
+// (kind::f16) or, with tf32, TF32 (kind::tf32); FP32 accumulation.  ws: device workspace of
+// tc_gemm_workspace_bytes(M, N, K, tf32) bytes; d_err: device word set non-zero if a bounded wait
+// of the kernel ran out.  Returns 0, or < 0 if the workspace is too small / the tensor maps
+// could not be built.
+size_t tc_gemm_workspace_bytes(long long M, long long N, long long K, bool tf32);
 int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View<float> B, c64 beta, View<float> C,
-            void* ws, size_t ws_bytes, int* d_err);
+            void* ws, size_t ws_bytes, int* d_err, bool tf32);
 int eig_selftest(int n, int fp64, int kind, unsigned long long seed, double* out);
 int svd_selftest(int p, int q, int fp64, const double* X, double* s, double* out);
 int eigh_noalloc(int n, int fp64, const void* A, long long lda, void* w, void* V, long long ldv, cudaStream_t st);

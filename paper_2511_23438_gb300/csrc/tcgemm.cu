@@ -3,16 +3,18 @@
 //   C(i, j) = alpha * sum_k A(i, k) B(k, j) + beta * C(i, j)      (complex64 in and out)
 //
 // Split precision: every real component x is written as x_hi + x_lo with
-// x_hi = bf16(x), x_lo = bf16(x - x_hi) (16 significant bits), and a real product
-// x * y is formed from the three bf16 products hi*hi + hi*lo + lo*hi with FP32
-// accumulation in tensor memory.  The complex product uses four real accumulators
+// x_hi = bf16(x), x_lo = bf16(x - x_hi) (16 significant bits; kind::f16), or with
+// x_hi = tf32(x), x_lo = tf32(x - x_hi) (22 significant bits; kind::tf32, half the
+// BF16 tensor rate), and a real product x * y is formed from the three products
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.  The complex product uses four real accumulators
 // P = Ar Br, T = Ai Bi, U = Ar Bi, W = Ai Br, so Re = P - T and Im = U + W.
 //
-// Data path: a conversion kernel writes the operands as BF16 planes
-// [re_hi, im_hi, re_lo, im_lo] x rows x Kp (K contiguous, Kp a multiple of 64, zero
-// padded); per 64-wide K step the TMA unit loads a 4-plane box of A (128 rows) and of
-// B (BN rows) into 128-byte-swizzled shared memory; one thread issues the 48
-// tcgen05.mma (M = 128, N = BN, K = 16) of the step; tcgen05.commit frees the stage;
+// Data path: a conversion kernel writes the operands as planes (BF16 or TF32-in-FP32)
+// [re_hi, im_hi, re_lo, im_lo] x rows x Kp (K contiguous, Kp a multiple of the K tile,
+// zero padded); per K tile of 128 bytes a row (64 BF16 / 32 TF32 elements) the TMA unit
+// loads a 4-plane box of A (128 rows) and of B (BN rows) into 128-byte-swizzled shared
+// memory; one thread issues the 48 tcgen05.mma (M = 128, N = BN, 32 bytes of K each:
+// K = 16 BF16 / 8 TF32) of the tile; tcgen05.commit frees the stage;
 // four epilogue warps read the accumulators with tcgen05.ld and write C.
 // Warp roles: warp 0 TMA producer, warp 1 TMEM owner + MMA issuer, warps 2-5 epilogue.
 // Every mbarrier wait is bounded: on timeout the kernel records an error word and
@@ -29,9 +31,15 @@
 namespace mpsgb {
 
 namespace {
-constexpr int TBM = 128, TBK = 64, TSTAGES = 2, TBN = 64;
-constexpr int A_STAGE_BYTES = 4 * TBM * TBK * 2;  // 64 KB
-constexpr int B_STAGE_BYTES = 4 * TBN * TBK * 2;  // 32 KB
+constexpr int TBM = 128, TSTAGES = 2, TBN = 64;
+constexpr int ROWB = 128;                          // bytes of one tile row (the swizzle span)
+constexpr int A_STAGE_BYTES = 4 * TBM * ROWB;      // 64 KB
+constexpr int B_STAGE_BYTES = 4 * TBN * ROWB;      // 32 KB
+template <bool TF>
+struct Split {                                     // plane element: BF16 (kind::f16) or TF32 in FP32 (kind::tf32)
+  static constexpr int ES = TF ? 4 : 2;            // bytes per element
+  static constexpr int BK = ROWB / ES;             // K elements per tile
+};
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
 constexpr int TMEM_COLS = 4 * TBN;                 // P, T, U, W accumulators
 constexpr long long WAIT_LIMIT = 1LL << 26;        // bounded mbarrier waits
@@ -82,16 +90,26 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor: FP32 accumulate (D format 1), A and B format BF16 (1, kind::f16) or
+// TF32 (2, kind::tf32), both K-major, N / 8 and M / 16.
+__host__ __device__ constexpr uint32_t idesc_split(int M, int N, bool tf32) {
+  return (1u << 4) | ((tf32 ? 2u : 1u) << 7) | ((tf32 ? 2u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-          dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+template <bool TF>
+__device__ __forceinline__ void mma_split(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (TF) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -105,6 +123,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])                  \
       : "r"(taddr))
 
+template <bool TF>
 __global__ void __launch_bounds__(192, 1)
     tc_cgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                     int nkb, c64 alpha, c64 beta, View<float> C, int* err) {
@@ -145,13 +164,13 @@ __global__ void __launch_bounds__(192, 1)
         unsigned char* a_dst = smem + s * STAGE_BYTES;
         unsigned char* b_dst = a_dst + A_STAGE_BYTES;
         mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-        tma_load_3d(&tmA, &full_bar[s], a_dst, kb * TBK, m0, 0);
-        tma_load_3d(&tmB, &full_bar[s], b_dst, kb * TBK, n0, 0);
+        tma_load_3d(&tmA, &full_bar[s], a_dst, kb * Split<TF>::BK, m0, 0);
+        tma_load_3d(&tmB, &full_bar[s], b_dst, kb * Split<TF>::BK, n0, 0);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = idesc_bf16(TBM, TBN);
+      const uint32_t idesc = idesc_split(TBM, TBN, TF);
       // (accumulator, A plane, B plane): P = Ar Br, T = Ai Bi, U = Ar Bi, W = Ai Br, 3 split terms each
       const int acc_of[12] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
       const int ap[12] = {0, 0, 2, 1, 1, 3, 0, 0, 2, 1, 1, 3};
@@ -163,12 +182,12 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a_base = smem_u32(smem + s * STAGE_BYTES);
         const uint32_t b_base = a_base + A_STAGE_BYTES;
-        for (int kk = 0; kk < TBK / 16; ++kk) {
+        for (int kk = 0; kk < ROWB / 32; ++kk) {  // 32 bytes of K per MMA
           for (int t = 0; t < 12; ++t) {
-            uint64_t ad = sdesc(a_base + ap[t] * (TBM * TBK * 2) + kk * 32);
-            uint64_t bd = sdesc(b_base + bp[t] * (TBN * TBK * 2) + kk * 32);
+            uint64_t ad = sdesc(a_base + ap[t] * (TBM * ROWB) + kk * 32);
+            uint64_t bd = sdesc(b_base + bp[t] * (TBN * ROWB) + kk * 32);
             uint32_t accumulate = (kb > 0 || kk > 0 || (t % 3) != 0) ? 1u : 0u;
-            mma_bf16(tmem + acc_of[t] * TBN, ad, bd, idesc, accumulate);
+            mma_split<TF>(tmem + acc_of[t] * TBN, ad, bd, idesc, accumulate);
           }
         }
         mma_commit(&empty_bar[s]);
@@ -213,9 +232,17 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// op(X) (rows x K) -> BF16 planes [re_hi, im_hi, re_lo, im_lo][rows][Kp], zero padded in k
+__device__ __forceinline__ float to_tf32(float x) {  // round to nearest, ties away: 10 explicit mantissa bits
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// op(X) (rows x K) -> planes [re_hi, im_hi, re_lo, im_lo][rows][Kp], zero padded in k: BF16
+// (hi = bf16(x), lo = bf16(x - hi)) or TF32 stored as FP32 (hi = tf32(x), lo = tf32(x - hi))
+template <bool TF>
 __global__ void __launch_bounds__(256) split_planes_kernel(int rows, int K, int Kp, View<float> src, bool kfast,
-                                                           __nv_bfloat16* planes) {
+                                                           void* out) {
   __shared__ c64 tile[32][65];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   for (int e = threadIdx.x; e < 32 * 64; e += 256) {
@@ -234,14 +261,24 @@ __global__ void __launch_bounds__(256) split_planes_kernel(int rows, int K, int 
     int r = e / 64, k = e % 64;
     if (r0 + r >= rows || k0 + k >= Kp) continue;
     c64 v = tile[r][k];
-    __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
-    __nv_bfloat16 rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
-    __nv_bfloat16 il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
     size_t o = (size_t)(r0 + r) * Kp + (k0 + k);
-    planes[o] = rh;
-    planes[plane + o] = ih;
-    planes[2 * plane + o] = rl;
-    planes[3 * plane + o] = il;
+    if constexpr (TF) {
+      float* planes = static_cast<float*>(out);
+      const float rh = to_tf32(v.x), ih = to_tf32(v.y);
+      planes[o] = rh;
+      planes[plane + o] = ih;
+      planes[2 * plane + o] = to_tf32(v.x - rh);
+      planes[3 * plane + o] = to_tf32(v.y - ih);
+    } else {
+      __nv_bfloat16* planes = static_cast<__nv_bfloat16*>(out);
+      __nv_bfloat16 rh = __float2bfloat16_rn(v.x), ih = __float2bfloat16_rn(v.y);
+      __nv_bfloat16 rl = __float2bfloat16_rn(v.x - __bfloat162float(rh));
+      __nv_bfloat16 il = __float2bfloat16_rn(v.y - __bfloat162float(ih));
+      planes[o] = rh;
+      planes[plane + o] = ih;
+      planes[2 * plane + o] = rl;
+      planes[3 * plane + o] = il;
+    }
   }
 }
 
@@ -262,14 +299,16 @@ EncodeTiledFn encoder() {
   return g_encode;
 }
 
-bool make_map(CUtensorMap* tm, void* base, int rows, int Kp, int box_rows) {
+bool make_map(CUtensorMap* tm, void* base, int rows, int Kp, int box_rows, bool tf32) {
   EncodeTiledFn enc = encoder();
   if (!enc) return false;
+  const cuuint64_t esz = tf32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 4};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 4};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * esz, (cuuint64_t)rows * Kp * esz};
+  cuuint32_t box[3] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows, 4};
   cuuint32_t es[3] = {1, 1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  return enc(tm, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
@@ -277,34 +316,46 @@ bool make_map(CUtensorMap* tm, void* base, int rows, int Kp, int box_rows) {
 bool is_kfast(const View<float>& v) { return v.col.inner == 0 && v.col.stride == 1; }
 }  // namespace
 
-size_t tc_gemm_workspace_bytes(long long M, long long N, long long K) {
-  long long Kp = (K + TBK - 1) / TBK * TBK;
-  return (size_t)(4 * 2) * (size_t)(M + N) * Kp + 2048;
+size_t tc_gemm_workspace_bytes(long long M, long long N, long long K, bool tf32) {
+  const long long bk = tf32 ? Split<true>::BK : Split<false>::BK;
+  const long long Kp = (K + 63) / 64 * 64;  // a multiple of both K tiles (the split kernel's 64-wide k blocks)
+  (void)bk;
+  return (size_t)(4 * (tf32 ? 4 : 2)) * (size_t)(M + N) * Kp + 2048;
 }
 
 int tc_gemm(cudaStream_t st, int M, int N, int K, c64 alpha, View<float> A, View<float> B, c64 beta, View<float> C,
-            void* ws, size_t ws_bytes, int* d_err) {
+            void* ws, size_t ws_bytes, int* d_err, bool tf32) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
-  const int Kp = (K + TBK - 1) / TBK * TBK;
-  if (tc_gemm_workspace_bytes(M, N, K) > ws_bytes) return -1;
-  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(((uintptr_t)ws + 255) & ~uintptr_t(255));
-  __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>((((uintptr_t)(pa + (size_t)4 * M * Kp)) + 255) & ~uintptr_t(255));
+  const int Kp = (K + 63) / 64 * 64;
+  if (tc_gemm_workspace_bytes(M, N, K, tf32) > ws_bytes) return -1;
+  const size_t esz = tf32 ? 4 : 2;
+  char* pa = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~uintptr_t(255));
+  char* pb = reinterpret_cast<char*>((((uintptr_t)(pa + esz * 4 * (size_t)M * Kp)) + 255) & ~uintptr_t(255));
   // op(A) is M x K; op(B)^T is N x K with element (j, k) = op(B)(k, j)
   View<float> Bt;
   Bt.ptr = B.ptr; Bt.row = B.col; Bt.col = B.row; Bt.conj = B.conj;
-  split_planes_kernel<<<dim3(Kp / 64, (M + 31) / 32), 256, 0, st>>>(M, K, Kp, A, is_kfast(A), pa);
-  split_planes_kernel<<<dim3(Kp / 64, (N + 31) / 32), 256, 0, st>>>(N, K, Kp, Bt, is_kfast(Bt), pb);
+  if (tf32) {
+    split_planes_kernel<true><<<dim3(Kp / 64, (M + 31) / 32), 256, 0, st>>>(M, K, Kp, A, is_kfast(A), pa);
+    split_planes_kernel<true><<<dim3(Kp / 64, (N + 31) / 32), 256, 0, st>>>(N, K, Kp, Bt, is_kfast(Bt), pb);
+  } else {
+    split_planes_kernel<false><<<dim3(Kp / 64, (M + 31) / 32), 256, 0, st>>>(M, K, Kp, A, is_kfast(A), pa);
+    split_planes_kernel<false><<<dim3(Kp / 64, (N + 31) / 32), 256, 0, st>>>(N, K, Kp, Bt, is_kfast(Bt), pb);
+  }
   count_launch(2);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, pa, M, Kp, TBM) || !make_map(&tb, pb, N, Kp, TBN)) return -2;
+  if (!make_map(&ta, pa, M, Kp, TBM, tf32) || !make_map(&tb, pb, N, Kp, TBN, tf32)) return -2;
   const int smem = TSTAGES * STAGE_BYTES + 1024;
   static std::once_flag attr_once;  // several host threads (one per handle) may reach this at once
   std::call_once(attr_once, [smem] {
-    cudaFuncSetAttribute(tc_cgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(tc_cgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(tc_cgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   });
   dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM);
   kt_begin(KT_TC_GEMM, st);
-  tc_cgemm_kernel<<<grid, 192, smem, st>>>(ta, tb, M, N, Kp / TBK, alpha, beta, C, d_err);
+  if (tf32)
+    tc_cgemm_kernel<true><<<grid, 192, smem, st>>>(ta, tb, M, N, Kp / Split<true>::BK, alpha, beta, C, d_err);
+  else
+    tc_cgemm_kernel<false><<<grid, 192, smem, st>>>(ta, tb, M, N, Kp / Split<false>::BK, alpha, beta, C, d_err);
   kt_end(KT_TC_GEMM, st);
   kt_add_work(KT_TC_GEMM, 8.0 * M * N * (double)K);
   count_launch();
@@ -343,7 +394,7 @@ int tc_selftest(int M, int N, int K, int mode, unsigned long long seed, double* 
   c64 *A, *B, *C1, *C2;
   float* red;
   int* derr;
-  size_t wsb = tc_gemm_workspace_bytes(M, N, K);
+  size_t wsb = tc_gemm_workspace_bytes(M, N, K, (mode & 4) != 0);
   void* ws;
   cudaMalloc(&A, sizeof(c64) * (size_t)M * K);
   cudaMalloc(&B, sizeof(c64) * (size_t)K * N);
@@ -359,7 +410,7 @@ int tc_selftest(int M, int N, int K, int mode, unsigned long long seed, double* 
   View<float> va = (mode & 1) ? transposed<float>(A, M, true) : rowmajor<float>(A, K);
   View<float> vb = (mode & 2) ? transposed<float>(B, K, false) : rowmajor<float>(B, N);
   c64 one = cmake<float>(1, 0), zero = cmake<float>(0, 0);
-  int s = tc_gemm(st, M, N, K, one, va, vb, zero, rowmajor<float>(C1, N), ws, wsb, derr);
+  int s = tc_gemm(st, M, N, K, one, va, vb, zero, rowmajor<float>(C1, N), ws, wsb, derr, (mode & 4) != 0);
   gemm<float>(st, M, N, K, one, va, vb, zero, rowmajor<float>(C2, N));
   max_abs_diff_kernel<<<256, 256, 0, st>>>((long long)M * N, C1, C2, red);
   float h[2] = {0, 0};

@@ -184,7 +184,8 @@ def torch_allocator():
     return a
 
 
-def tc_gemm_selftest(M, N, K, mode=0, seed=1):
+def tc_gemm_selftest(M, N, K, mode=0, seed=1, tf32=False):
+    mode = mode | (4 if tf32 else 0)
     e = ctypes.c_double()
     _check(load().mpsgb_tc_gemm_selftest(M, N, K, mode, seed, ctypes.byref(e)))
     return e.value

@@ -19,8 +19,9 @@ from oracle import statevector as sv
 pytestmark = pytest.mark.gpu
 TOL = 1e-9
 TH3 = {k: model.initial_theta(v, coordination=model.COORDINATION_3D) for k, v in model.TEMPERATURES_3D.items()}
-# observables and |dF/F| of the split form (complex64 storage, FP32 truncation core)
-SPLIT_3D_BOUND = 1e-4
+# observables and |dF/F| of the split form (complex64 storage, FP32 truncation core): measured on a
+# GB300 at most 9.0e-5 (|d obs|, exact chi, five steps) and 7.6e-5 (|dF/F|, 3x3x4 chi = 32)
+SPLIT_3D_BOUND = 3e-4
 
 
 @pytest.fixture(scope="module")
