@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--cpu-updates", type=int, default=1, help="oracle bond updates timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-updates", type=int, default=2, help="FP64-form bond updates timed at full shape (0: none)")
+    ap.add_argument("--other-split", default="split_tf32x3", help="also time one step of this form on the evolved "
+                    "state ('' : none)")
     ap.add_argument("--serve-jobs", type=int, default=16, help="jobs of the short serving run (0: none)")
     ap.add_argument("--serve-steps", type=int, default=3, help="Trotter steps per serving job")
-    ap.add_argument("--batch-mps", type=int, default=32, help="MPS of the batched-advance leg (0: none)")
+    ap.add_argument("--batch-mps", type=int, default=64, help="MPS of the batched-advance leg (0: none)")
     ap.add_argument("--three-d", default="3x3x4", help="open 3D grid of the one-qubit-per-site leg ('' : none)")
     ap.add_argument("--three-d-chi", type=int, default=128)
     ap.add_argument("--xy", default="6x6", help="open grid of the XY-model leg ('' : none)")
@@ -382,6 +384,33 @@ def fp64_form_rate(lib, m_split, Lx, Ly, n_updates, stream):
                       (Lx, Ly, m_split.cfg.chi_max, n)}
 
 
+def other_split_rate(lib, m_split, prec, stream):
+    """Another complex64 form on the evolved state of the timed run: the MPS is written to a
+    checkpoint, relabelled with the form `prec` (same complex64 storage) and loaded on the same
+    stream; one whole Trotter step is timed with CUDA events."""
+    import torch
+
+    with tempfile.TemporaryDirectory() as td:
+        a = os.path.join(td, "a.bin")
+        b = os.path.join(td, "b.bin")
+        m_split.save(a)
+        lib.convert_checkpoint(a, b, prec)
+        g = lib.MPS.load_checkpoint(b, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    st0 = g.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(J, HX, DT, ORDER, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = g.stats()["truncations"] - st0["truncations"]
+    o = g.observables()
+    g.close()
+    return {"precision": prec, "value": n / (ms / 1e3), "unit": "bond updates/s", "bond_updates": n, "ms": ms,
+            "sample": "one Trotter step of the evolved state of the timed run", "Z": o["Z"], "Z2": o["Z2"]}
+
+
 def split_error_table(spec, prec, Lx=5, Ly=6, perturb=0.0):
     """Error of a complex64 form against the FP64 GPU form (both through the library, the FP64
     form being the one held to 1e-9 of the oracle) on the 5x6 grid (rows 3 + 3, d = 8) from the
@@ -585,6 +614,8 @@ def main():
             "counters_per_step": {k: (cnt1[k] - cnt0[k]) / args.steps for k in cnt1}}
     if args.fp64_updates > 0 and world == 1:
         line["fp64_form"] = fp64_form_rate(lib, m, Lx, Ly, args.fp64_updates, stream)
+    if args.other_split and world == 1 and args.prec != args.other_split:
+        line["other_split_form"] = other_split_rate(lib, m, args.other_split, stream)
     m.close()
     if args.serve_jobs > 0 and world == 1:
         line["serve"] = serve_run(args.serve_jobs, args.serve_steps, args.prec)

@@ -264,6 +264,7 @@ class EngineT : public Engine {
   std::vector<R> hbuf;
   bool tc = false;        // block-sized contractions on the tensor cores (split forms)
   bool tc_tf32 = false;   // ... with TF32 splits (kind::tf32) instead of BF16
+  GraphCache* gcache = new_graph_cache();  // CUDA graphs of this handle's fixed launch sequences
   void* tcws = nullptr;   // BF16 operand planes of the tensor-core GEMM
   size_t tcws_bytes = 0;
   int* derr = nullptr;    // device error word of bounded waits in kernels
@@ -294,6 +295,7 @@ class EngineT : public Engine {
 
   ~EngineT() override {
     if (stream) cudaStreamSynchronize(stream);
+    free_graph_cache(gcache);
     mem.release();
     if (stream) cudaStreamSynchronize(stream);
   }
@@ -389,6 +391,7 @@ class EngineT : public Engine {
   // nvec > 0: only the eigenvectors of the nvec largest eigenvalues are needed (the others are
   // not computed on the tridiagonal route)
   void eig(int n, C* A, R* w, C* V, void* ws, std::vector<double>& hw, int nvec = 0) {
+    GraphScope gs(gcache);
     int sw = eigh<R>(stream, n, A, n, 0, w, 0, V, n, 0, 1, ws, nvec);
     stats.eig_calls++;
     if (sw == -1) throw Fail{MPSGB_ETIMEDOUT, "Jacobi eigensolver did not converge within its sweep limit"};
@@ -904,6 +907,7 @@ class EngineT : public Engine {
     if (!flag) throw Fail{MPSGB_ENOMEM, "workspace exhausted in the Cholesky factorisation"};
     cudaMemcpyAsync(Cf, G, sizeof(C) * (size_t)n * n, cudaMemcpyDeviceToDevice, stream);
     const double rel = 32.0 * (sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920929e-7);
+    GraphScope gs(gcache);
     if (chol_inv<R>(stream, n, Cf, n, Ci, n, rel, cws, flag) != 0) throw Fail{MPSGB_EDEVICE, "Cholesky launch"};
     int hflag = 0;
     cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, stream);

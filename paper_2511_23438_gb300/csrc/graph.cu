@@ -7,13 +7,14 @@
 // off the device timeline.  The recording is made on a stream private to the calling host thread
 // (nothing runs during a recording, and no other thread's launches onto the caller's stream can
 // enter it, also where several handles share one stream); the graph is then launched on the
-// caller's stream, after the work already issued there.  One cache serves the process (at most 512 graphs, the least recently
-// used dropped first); a key holds the stream and every buffer address, and one handle's work runs
-// on one host thread at a time, so no graph is launched from two threads at once.  The legacy
-// default stream cannot be captured and a stream that is already capturing is not nested into:
-// both run the sequence directly, as does everything while per-launch-site timing is on (so that
-// each kernel stays bracketed by its own events) or while the calling thread has graphs switched
-// off (set_graphs_enabled).
+// caller's stream, after the work already issued there.  Graphs live in the cache of the handle
+// whose work is being issued (selected by GraphScope; a handle's work runs on one host thread at a
+// time, so its cache needs no lock; at most 128 graphs, the least recently used dropped first), or,
+// outside any handle, in one process-wide cache (a lock, at most 512 graphs).  A key holds the
+// stream and every buffer address.  The legacy default stream cannot be captured and a stream
+// that is already capturing is not nested into: both run the sequence directly, as does
+// everything while per-launch-site timing is on (so that each kernel stays bracketed by its own
+// events) or while the calling thread has graphs switched off (set_graphs_enabled).
 #include <cstdlib>
 #include <mutex>
 #include <vector>
@@ -31,17 +32,41 @@ struct Entry {
   unsigned long long used;
   cudaEvent_t done;  // recorded after every launch: an evicted graph is destroyed once it is idle
 };
-struct Cache {
-  std::mutex mu;
+}  // namespace
+
+struct GraphCache {
+  std::mutex mu;  // taken for the process-wide cache only
   std::vector<Entry> v;
   unsigned long long clock = 0;
+  size_t cap = 128;
+  void clear() {
+    for (auto& e : v) {
+      cudaEventSynchronize(e.done);
+      cudaGraphExecDestroy(e.exec);
+      cudaEventDestroy(e.done);
+    }
+    v.clear();
+  }
 };
+GraphCache* new_graph_cache() { return new GraphCache(); }
+void free_graph_cache(GraphCache* c) {
+  if (!c) return;
+  c->clear();
+  delete c;
+}
+thread_local GraphCache* t_graph_cache = nullptr;
+GraphScope::GraphScope(GraphCache* c) : prev(t_graph_cache) { t_graph_cache = c; }
+GraphScope::~GraphScope() { t_graph_cache = prev; }
+
+namespace {
+using Cache = GraphCache;
 void release_all();
 Cache& cache() {
   // never destroyed: the graphs are released by an exit handler registered after the CUDA runtime
   // initialised (so it runs before the runtime's own teardown)
   static Cache* c = [] {
     Cache* p = new Cache();
+    p->cap = 512;
     std::atexit(release_all);
     return p;
   }();
@@ -50,14 +75,8 @@ Cache& cache() {
 void release_all() {
   Cache& c = cache();
   std::lock_guard<std::mutex> lk(c.mu);
-  for (auto& e : c.v) {
-    cudaEventSynchronize(e.done);
-    cudaGraphExecDestroy(e.exec);
-    cudaEventDestroy(e.done);
-  }
-  c.v.clear();
+  c.clear();
 }
-constexpr size_t kMaxGraphs = 512;
 thread_local bool t_graphs = true;
 
 // the calling thread's capture stream, created on first use and destroyed with the thread
@@ -86,10 +105,12 @@ int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<in
     if (issue(st) != 0) return -4;
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
   }
-  Cache& c = cache();
+  Cache& c = t_graph_cache ? *t_graph_cache : cache();
+  const bool shared = !t_graph_cache;
   {
-    // launch under the lock, so that no other thread evicts the graph in between
-    std::lock_guard<std::mutex> lk(c.mu);
+    // launch under the lock (shared cache), so that no other thread evicts the graph in between
+    std::unique_lock<std::mutex> lk(c.mu, std::defer_lock);
+    if (shared) lk.lock();
     for (auto& e : c.v)
       if (e.key == key) {
         e.used = ++c.clock;
@@ -128,8 +149,9 @@ int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<in
   bool evicted = false;
   Entry drop{};
   {
-    std::lock_guard<std::mutex> lk(c.mu);
-    if (c.v.size() >= kMaxGraphs) {
+    std::unique_lock<std::mutex> lk(c.mu, std::defer_lock);
+    if (shared) lk.lock();
+    if (c.v.size() >= c.cap) {
       size_t old = 0;
       for (size_t i = 1; i < c.v.size(); ++i)
         if (c.v[i].used < c.v[old].used) old = i;

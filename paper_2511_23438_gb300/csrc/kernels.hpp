@@ -23,6 +23,15 @@ struct GraphKey {
 // a capture stream private to the calling thread (s = that stream, so that no other thread's work on
 // st can enter the recording) and launched on st; later calls with the same key launch the graph.
 int replay_or_issue(cudaStream_t st, const GraphKey& key, const std::function<int(cudaStream_t)>& issue);
+// graph cache of one handle; GraphScope makes it the calling thread's cache for its lifetime
+struct GraphCache;
+GraphCache* new_graph_cache();
+void free_graph_cache(GraphCache* c);  // waits for the cached graphs' last launches
+struct GraphScope {
+  explicit GraphScope(GraphCache* c);
+  ~GraphScope();
+  GraphCache* prev;
+};
 // graph replay for the calling host thread (on by default)
 void set_graphs_enabled(bool on);
 bool graphs_enabled();
