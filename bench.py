@@ -58,7 +58,10 @@ def parse():
     ap.add_argument("--three-d", default="3x3x4", help="open 3D grid of the one-qubit-per-site leg ('' : none)")
     ap.add_argument("--three-d-chi", type=int, default=128)
     ap.add_argument("--xy", default="6x6", help="open grid of the XY-model leg ('' : none)")
-    ap.add_argument("--xy-chi", type=int, default=256)
+    ap.add_argument("--xy-chi", type=int, default=64)
+    ap.add_argument("--save-state", default="", help="write the evolved MPS of the timed run to this checkpoint")
+    ap.add_argument("--one-gate", default="", help="load this checkpoint, apply one adjacent gate between the "
+                    "middle blocks (a single bond-update unit of the step, for launch lists), print it and exit")
     ap.add_argument("--peaks", action="store_true", help="measure dense matmul rates (torch) and exit")
     ap.add_argument("--split-error", default="", help="error table of the complex64 forms against the FP64 GPU "
                     "form: comma-separated chi:steps pairs on the 5x6 grid (e.g. 64:20,256:8), then exit")
@@ -384,6 +387,29 @@ def fp64_form_rate(lib, m_split, Lx, Ly, n_updates, stream):
                       (Lx, Ly, m_split.cfg.chi_max, n)}
 
 
+def one_gate(path, Lx, Ly):
+    """One bond-update unit of the bench step on a saved state: the checkpoint is loaded on a
+    stream of its own and the first adjacent gate between the middle blocks is applied once;
+    device time by CUDA events, launches by the library's counter."""
+    import torch
+    from paper_2511_23438_gb300 import lib
+    lib.load()
+    s = torch.cuda.Stream()
+    g = lib.MPS.load_checkpoint(path, stream=s.cuda_stream)
+    gates = middle_adjacent_gates(lib.schedule_gates(Lx, Ly), Lx)
+    torch.cuda.synchronize()
+    l0, u0 = lib.launch_count(), g.stats()["truncations"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    g.apply_gates(gates[0], 1, J * DT)
+    e1.record(s)
+    torch.cuda.synchronize()
+    out = {"one_gate_ms": e0.elapsed_time(e1), "launches": lib.launch_count() - l0,
+           "bond_updates": g.stats()["truncations"] - u0, "launches_before": l0}
+    g.close()
+    return out
+
+
 def other_split_rate(lib, m_split, prec, stream):
     """Another complex64 form on the evolved state of the timed run: the MPS is written to a
     checkpoint, relabelled with the form `prec` (same complex64 storage) and loaded on the same
@@ -468,6 +494,9 @@ def main():
         return
     if args.peaks:
         print(json.dumps(measure_peaks()), flush=True)
+        return
+    if args.one_gate:
+        print(json.dumps(one_gate(args.one_gate, Lx, Ly)), flush=True)
         return
     if args.split_error:
         print(json.dumps(split_error_table(args.split_error, args.prec, perturb=args.split_perturb)), flush=True)
@@ -612,6 +641,8 @@ def main():
             "kernel_sites_tflops": {k: round(v[2] / (v[0] / 1e3) / 1e12, 3) for k, v in ktimes.items()
                                     if v[0] > 0 and v[2] > 0 and "in-block" not in k},
             "counters_per_step": {k: (cnt1[k] - cnt0[k]) / args.steps for k in cnt1}}
+    if args.save_state and world == 1:
+        m.save(args.save_state)
     if args.fp64_updates > 0 and world == 1:
         line["fp64_form"] = fp64_form_rate(lib, m, Lx, Ly, args.fp64_updates, stream)
     if args.other_split and world == 1 and args.prec != args.other_split:
