@@ -608,6 +608,11 @@ def main():
                  "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
+        if "hetrd" in name and args.prec != "fp64" and args.chi == 1024:
+            # ncu DRAM bytes (read + write) of one n = 2048 complex64 launch, the core size of this
+            # configuration (the matrix is read from HBM once)
+            r["traffic"] = 34.56e6
+            r["traffic_case"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one n = 2048 launch"
         r["kernel"] = name
         r["launches"] = kn
         r["avg_launch_ms"] = kms / max(1, kn)
