@@ -86,17 +86,12 @@ __device__ __forceinline__ void grid_wait(unsigned* count, unsigned target, int*
 //      vector into column i of W (global) for the back-transformation, and the wait on
 //      barrier 2, whose latency the update hides (the next column only needs colbuf).
 // acc[0..1]: squared norm of column i (parity i & 1); acc[2..5]: p^H v (re, im) by parity.
-// partial sums per CTA: active rows x segments <= owned rows + warps (segments only when a CTA owns
-// fewer active rows than warps); the host checks ceil(n / grid) + 16 <= MV_PARTS
-constexpr int MV_PARTS = 256;
-
 template <typename R>
 __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long long lda, Cx<R>* W, R* d, R* e,
                                                     Cx<R>* tau, Cx<R>* pb, Cx<R>* colbuf, double* acc, unsigned* bar,
                                                     int* err, long long lim, int s_fit) {
   extern __shared__ __align__(16) unsigned char hetrd_smem[];
   __shared__ double hsc[6];  // tau (re, im), 1 / (alpha - beta) (re, im), a2 (re, im)
-  __shared__ Cx<R> mvpart[MV_PARTS];  // segment partial sums of the matrix-vector product
   Cx<R>* vs = reinterpret_cast<Cx<R>*>(hetrd_smem);
   Cx<R>* ps = vs + n;
   Cx<R>* rs = ps + n;  // s_fit cached rows
@@ -139,12 +134,11 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
       } else {
         const double nrm_all = sqrt(ar * ar + ai * ai + xn2);
         beta = ar >= 0 ? -nrm_all : nrm_all;
-        const double ib = 1.0 / beta;  // two reciprocals instead of four divisions
-        tr = (beta - ar) * ib;
-        ti = -ai * ib;
-        const double dr = ar - beta, di = ai, iden = 1.0 / (dr * dr + di * di);  // scale = 1 / (alpha - beta)
-        sr = dr * iden;
-        si = -di * iden;
+        tr = (beta - ar) / beta;
+        ti = -ai / beta;
+        const double dr = ar - beta, di = ai, den = dr * dr + di * di;  // scale = 1 / (alpha - beta)
+        sr = dr / den;
+        si = -di / den;
       }
       hsc[0] = tr; hsc[1] = ti; hsc[2] = sr; hsc[3] = si;
       if (c == 0) {
@@ -159,43 +153,28 @@ __global__ void __launch_bounds__(512) hetrd_kernel(int n, const Cx<R>* A, long 
     __syncthreads();
     const int s0 = i + 1 <= c ? 0 : (i + 1 - c + G - 1) / G;  // first slot with a row >= i + 1
     {
-      // p_r = tau (W22 v)_r for the owned rows: each row is cut into nseg segments so that all warps
-      // take part even when a CTA owns fewer active rows than it has warps (rows kept in global
-      // memory are latency-bound); the segments' partial sums are added in order
-      const int nact = nslots - s0;
-      const int len = n - (i + 1);
-      int nseg = nact > 0 ? (nw + nact - 1) / nact : 1;
-      nseg = nseg > 8 ? 8 : nseg;
-      const int seglen = ((len + nseg - 1) / nseg + 31) / 32 * 32;
-      for (int item = warp; item < nact * nseg; item += nw) {
-        const int k = item / nseg, seg = item - k * nseg;
-        const Cx<R>* row = rowp(s0 + k);
-        const int j0 = i + 1 + seg * seglen;
-        const int j1 = j0 + seglen < n ? j0 + seglen : n;
+      double dre = 0, dim = 0;
+      for (int slot = s0 + warp; slot < nslots; slot += nw) {
+        const int r = c + slot * G;
+        const Cx<R>* row = rowp(slot);
         Cx<R> sacc = cmake<R>(0, 0);
-#pragma unroll 8
-        for (int j = j0 + lane; j < j1; j += 32) cfma(sacc, row[j], vs[j]);
+#pragma unroll 16
+        for (int j = i + 1 + lane; j < n; j += 32) cfma(sacc, row[j], vs[j]);
         R sr = sacc.x, si = sacc.y;
         for (int o = 16; o > 0; o >>= 1) {
           sr += __shfl_xor_sync(0xffffffffu, sr, o);
           si += __shfl_xor_sync(0xffffffffu, si, o);
         }
-        if (lane == 0) mvpart[item] = cmake<R>(sr, si);
+        if (lane == 0) {
+          const Cx<R> pv = tv * cmake<R>(sr, si);
+          pb[r] = pv;
+          ps[r] = pv;
+          const Cx<R> v = vs[r];
+          dre += (double)pv.x * v.x + (double)pv.y * v.y;  // conj(p) v
+          dim += (double)pv.x * v.y - (double)pv.y * v.x;
+        }
       }
-      __syncthreads();
-      double dre = 0, dim = 0;
-      for (int k = t; k < nact; k += nt) {
-        const int r = c + (s0 + k) * G;
-        Cx<R> sum = cmake<R>(0, 0);
-        for (int seg = 0; seg < nseg; ++seg) sum = sum + mvpart[k * nseg + seg];
-        const Cx<R> pv = tv * sum;
-        pb[r] = pv;
-        ps[r] = pv;
-        const Cx<R> v = vs[r];
-        dre += (double)pv.x * v.x + (double)pv.y * v.y;  // conj(p) v
-        dim += (double)pv.x * v.y - (double)pv.y * v.x;
-      }
-      if (dre != 0 || dim != 0) {
+      if (lane == 0 && (dre != 0 || dim != 0)) {
         atomicAdd(&acc[2 + 2 * par], dre);
         atomicAdd(&acc[3 + 2 * par], dim);
       }
@@ -684,7 +663,6 @@ int eigh_tridiag(cudaStream_t st, int n, const Cx<R>* A, long long lda, R* w, Cx
   // reductions of other handles (other streams) at the same time
   int grid = std::min(sms, std::max(16, (n + 11) / 12));
   const int slots = (n + grid - 1) / grid;
-  if (slots + 16 > MV_PARTS) return -4;  // the kernel's per-CTA segment partial sums
   int s_fit = (int)std::min<size_t>((size_t)slots, (smem_cap - 2 * row_bytes) / row_bytes);
   const size_t hsm = (2 + (size_t)s_fit) * row_bytes;
   // the attribute is a property of the kernel, shared by every host thread: it is raised once to
