@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--three-d", default="3x3x4", help="open 3D grid of the one-qubit-per-site leg ('' : none)")
     ap.add_argument("--three-d-chi", type=int, default=128)
     ap.add_argument("--xy", default="6x6", help="open grid of the XY-model leg ('' : none)")
-    ap.add_argument("--xy-chi", type=int, default=64)
+    ap.add_argument("--xy-chi", type=int, default=32)
     ap.add_argument("--save-state", default="", help="write the evolved MPS of the timed run to this checkpoint")
     ap.add_argument("--one-gate", default="", help="load this checkpoint, apply one adjacent gate between the "
                     "middle blocks (a single bond-update unit of the step, for launch lists), print it and exit")
