@@ -384,6 +384,8 @@ class MPS:
 
 
 def batch_step(mps_list, nlayers, use_graph=1):
+    """nlayers Trotter steps of every handle, concurrently (mpsgb_batch_step); use_graph = 1 replays
+    the fixed launch sequences as CUDA graphs on handles with a stream of their own."""
     arr = (ctypes.c_void_p * len(mps_list))(*[m.h.value if isinstance(m.h, ctypes.c_void_p) else m.h
                                               for m in mps_list])
     _check(load().mpsgb_batch_step(arr, len(mps_list), nlayers, use_graph))
