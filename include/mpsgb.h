@@ -328,6 +328,12 @@ double mpsgb_initial_theta_lattice(mpsgb_lattice lattice, double J, double hx, d
  * (dtheta = 0), 1 = mid (2 pi/9), 2 = high (3 pi/9).  Returns NaN for another temperature. */
 double mpsgb_gamma_fit(int temperature, int chi, int n);
 
+/* Host-only: gamma_fit for a lattice: LATTICE_2D_GROUPED as mpsgb_gamma_fit; LATTICE_3D_SITES from
+ * Table 3d_gamma_scaling of the Supplemental Material's 3D section (a = 2.654, 2.153, 1.5104 for
+ * dtheta = 0, pi/9, 2 pi/9; b = 0).  NaN for another lattice, temperature outside 0..2 or
+ * chi, n < 1. */
+double mpsgb_gamma_fit_lattice(mpsgb_lattice lattice, int temperature, int chi, int n);
+
 /* Host-only rescaling (Eq. Z_tot_via_F and Eq. z2_tot_rescaled): out[0] = F * z,
  * out[1] = z2 * F^gamma. */
 int mpsgb_rescale(double z, double z2, double F, double gamma, double out[2]);

@@ -369,6 +369,15 @@ double mpsgb_gamma_fit(int temperature, int chi, int n) {
   return a[temperature] * std::log2((double)chi) / n + b[temperature];
 }
 
+double mpsgb_gamma_fit_lattice(mpsgb_lattice lattice, int temperature, int chi, int n) {
+  if (lattice == MPSGB_LATTICE_2D_GROUPED) return mpsgb_gamma_fit(temperature, chi, n);
+  if (lattice != MPSGB_LATTICE_3D_SITES) return std::nan("");
+  // Table 3d_gamma_scaling: (a, b) for low / mid / high (b = 0 throughout)
+  static const double a[3] = {2.654, 2.153, 1.5104};
+  if (temperature < 0 || temperature > 2 || chi < 1 || n < 1) return std::nan("");
+  return a[temperature] * std::log2((double)chi) / n;
+}
+
 int mpsgb_rescale(double z, double z2, double F, double gamma, double out[2]) {
   if (!out) return fail(MPSGB_EINVAL, "null argument");
   out[0] = F * z;

@@ -86,6 +86,7 @@ _SIGS = {
     "mpsgb_eigh_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     "mpsgb_initial_theta": (ctypes.c_double, [ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "mpsgb_gamma_fit_lattice": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mpsgb_initial_theta_lattice": (ctypes.c_double, [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "mpsgb_config_schedule_info": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_longlong)]),
     "mpsgb_config_schedule_gates": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -228,8 +229,10 @@ def initial_theta(J, h, dtheta, lattice=None):
     return load().mpsgb_initial_theta_lattice(lattice, J, h, dtheta)
 
 
-def gamma_fit(temperature, chi, n):
-    return load().mpsgb_gamma_fit(temperature, chi, n)
+def gamma_fit(temperature, chi, n, lattice=None):
+    if lattice is None:
+        return load().mpsgb_gamma_fit(temperature, chi, n)
+    return load().mpsgb_gamma_fit_lattice(lattice, temperature, chi, n)
 
 
 def rescale(z, z2, F, gamma):

@@ -95,6 +95,12 @@ def test_host_formulas(lib):
         for chi, n in [(64, 30), (1024, 48), (4096, 56)]:
             assert abs(lib.gamma_fit(t, chi, n) - rescale.gamma_fit(name, chi, n)) < 1e-15
     assert math.isnan(lib.gamma_fit(3, 64, 30))
+    for t, name in enumerate(("low", "mid", "high")):
+        for chi, n in [(64, 36), (256, 64), (1024, 36)]:
+            g3 = lib.gamma_fit(t, chi, n, lattice=lib.LATTICE_3D_SITES)
+            assert abs(g3 - rescale.gamma_fit(name, chi, n, three_d=True)) < 1e-15
+            assert lib.gamma_fit(t, chi, n, lattice=lib.LATTICE_2D_GROUPED) == lib.gamma_fit(t, chi, n)
+    assert math.isnan(lib.gamma_fit(0, 64, 36, lattice=lib.LATTICE_2D_SITES))
     z, z2 = lib.rescale(0.3, 0.2, 0.5, 0.7)
     assert abs(z - rescale.rescale_z(0.3, 0.5)) < 1e-16
     assert abs(z2 - rescale.rescale_z2(0.2, 0.5, 0.7)) < 1e-16

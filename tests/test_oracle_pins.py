@@ -371,6 +371,15 @@ def test_gamma_table_matches_paper_golden():
     assert abs(rescale.gamma_fit("high", 2, 1) - (1.641 - 0.1298)) < 1e-15
 
 
+def test_gamma_table_3d_matches_paper_golden():
+    with open(os.path.join(GOLDEN, "gamma_scaling_3d.json")) as fh:
+        gold = json.load(fh)
+    for t in ("low", "mid", "high"):
+        assert rescale.GAMMA_TABLE_3D[t] == (gold[t]["a"], gold[t]["b"])
+    # mid, chi = 256, n = 36 (the paper's 3x3x4 lattice): 2.153 * 8 / 36
+    assert abs(rescale.gamma_fit("mid", 256, 36, three_d=True) - 2.153 * 8 / 36) < 1e-15
+
+
 def test_rescaling_limits():
     # F -> 1 leaves observables unchanged; gamma = 1 reduces Eq. z2_tot_rescaled to F scaling
     assert rescale.rescale_z(0.3, 1.0) == 0.3
